@@ -1,0 +1,205 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module holds only the *problem definitions* (initial data sampled at the grid
+positions and, for the Alfven wave, its exact solution).  It holds none of the
+method's arithmetic: no reconstruction, flux, inversion or derivative.  The
+conserved variables and the staggered field are built from these inputs by each
+implementation on its own side (the CUDA library and the CPU oracle alike).
+
+Grid convention (periodic, x fastest, arrays ``[var, nz, ny, nx]``):
+  cell (i,j,k) at ((i+1/2)hx, (j+1/2)hy, (k+1/2)hz);
+  face array d: the face half a cell above the cell centre along d;
+  edge array c: the edge half a cell above the cell centre along both
+  directions other than c (A_x at (i, j+1/2, k+1/2) and cyclic).
+"""
+import math
+
+import numpy as np
+
+GAMMA = 4.0 / 3.0
+
+
+def _coords(nx, ny, nz, lx, ly, lz, off):
+    """Positions of samples offset by ``off`` = (ox, oy, oz) cells from the lower
+    cell corner; returns arrays broadcastable to [nz, ny, nx]."""
+    hx, hy, hz = lx / nx, ly / ny, lz / nz
+    x = (np.arange(nx) + off[0]) * hx
+    y = (np.arange(ny) + off[1]) * hy
+    z = (np.arange(nz) + off[2]) * hz
+    return x[None, None, :], y[None, :, None], z[:, None, None]
+
+
+# ---------------------------------------------------------------------------
+# Circularly polarised Alfven wave (the paper's CPA-3D test, Sec. 4)
+# ---------------------------------------------------------------------------
+
+def alfven_speed(rho=1.0, p=1.0, B0=1.0, eta=1.0, gam=GAMMA):
+    """Speed of the exact large-amplitude circularly polarised relativistic Alfven
+    wave (Sec. 4, the v_A^2 equation): with E = rho h + B0^2 (1 + eta^2),
+    v_A^2 = (B0^2 / E) / [ (1 + sqrt(1 - (2 eta B0^2 / E)^2)) / 2 ]."""
+    rhoh = rho + gam / (gam - 1.0) * p
+    e = rhoh + B0 * B0 * (1.0 + eta * eta)
+    q = 2.0 * eta * B0 * B0 / e
+    va2 = (B0 * B0 / e) / (0.5 * (1.0 + math.sqrt(1.0 - q * q)))
+    return math.sqrt(va2)
+
+
+def cpa_frame(kvec):
+    """Right-handed orthonormal frame (X, Y, Z) with X along k.  Y = e x X / |e x X|
+    with e = z (or x when k is along z), Z = X x Y.  For k along (1,1,1) this gives
+    Y = (-1, 1, 0)/sqrt(2)."""
+    X = np.asarray(kvec, dtype=np.float64)
+    X = X / np.linalg.norm(X)
+    e = np.array([0.0, 0.0, 1.0])
+    if abs(abs(X[2]) - 1.0) < 1e-12:
+        e = np.array([1.0, 0.0, 0.0])
+    Y = np.cross(e, X)
+    Y /= np.linalg.norm(Y)
+    Z = np.cross(X, Y)
+    return X, Y, Z
+
+
+class CPA:
+    """Circularly polarised Alfven wave along k = 2 pi (mx/lx, my/ly, mz/lz):
+    B = B0 X + eta B0 (Y cos xi + Z sin xi), v = -v_A eta (Y cos xi + Z sin xi),
+    rho and p uniform, xi = k.x - |k| v_A t (Sec. 4).  The transverse field is given
+    through the edge vector potential A = -(eta B0/|k|) (Y cos xi + Z sin xi),
+    whose curl is exactly the transverse part of B."""
+
+    def __init__(self, nx, ny, nz, m=(1, 0, 0), L=(1.0, 1.0, 1.0), rho=1.0, p=1.0,
+                 B0=1.0, eta=1.0, gam=GAMMA):
+        self.n = (nx, ny, nz)
+        self.L = tuple(float(v) for v in L)
+        self.k = 2.0 * math.pi * np.array([m[0] / L[0], m[1] / L[1], m[2] / L[2]])
+        self.kmag = float(np.linalg.norm(self.k))
+        self.X, self.Y, self.Z = cpa_frame(self.k)
+        self.rho, self.p, self.B0, self.eta, self.gam = rho, p, B0, eta, gam
+        self.vA = alfven_speed(rho, p, B0, eta, gam)
+        self.period = 2.0 * math.pi / (self.kmag * self.vA)
+
+    def _phase(self, off, t):
+        x, y, z = _coords(*self.n, *self.L, off)
+        return self.k[0] * x + self.k[1] * y + self.k[2] * z - self.kmag * self.vA * t
+
+    def prim5(self, t=0.0):
+        """[5, nz, ny, nx]: rho, vx, vy, vz, p at cell centres."""
+        nx, ny, nz = self.n
+        xi = np.broadcast_to(self._phase((0.5, 0.5, 0.5), t), (nz, ny, nx))
+        out = np.empty((5, nz, ny, nx))
+        out[0] = self.rho
+        out[4] = self.p
+        c, s = np.cos(xi), np.sin(xi)
+        for d in range(3):
+            out[1 + d] = -self.vA * self.eta * (self.Y[d] * c + self.Z[d] * s)
+        return out
+
+    def bface_background(self):
+        """[3, nz, ny, nx]: the uniform part B0 X on every face."""
+        nx, ny, nz = self.n
+        out = np.empty((3, nz, ny, nx))
+        for d in range(3):
+            out[d] = self.B0 * self.X[d]
+        return out
+
+    def apot(self, t=0.0):
+        """[3, nz, ny, nx]: edge vector potential of the transverse field."""
+        nx, ny, nz = self.n
+        offs = [(0.5, 1.0, 1.0), (1.0, 0.5, 1.0), (1.0, 1.0, 0.5)]
+        out = np.empty((3, nz, ny, nx))
+        amp = -self.eta * self.B0 / self.kmag
+        for c in range(3):
+            xi = np.broadcast_to(self._phase(offs[c], t), (nz, ny, nx))
+            out[c] = amp * (self.Y[c] * np.cos(xi) + self.Z[c] * np.sin(xi))
+        return out
+
+    def exact_prim8(self, t):
+        """[8, nz, ny, nx]: exact rho, v, p and B at cell centres at time t."""
+        nx, ny, nz = self.n
+        out = np.empty((8, nz, ny, nx))
+        out[:5] = self.prim5(t)
+        xi = np.broadcast_to(self._phase((0.5, 0.5, 0.5), t), (nz, ny, nx))
+        c, s = np.cos(xi), np.sin(xi)
+        for d in range(3):
+            out[5 + d] = self.B0 * self.X[d] + self.eta * self.B0 * (self.Y[d] * c + self.Z[d] * s)
+        return out
+
+    def state_along(self, xi):
+        """Primitives and field on the wave as functions of the phase xi (1-D arrays):
+        returns prim[5, m], B[3, m]."""
+        xi = np.asarray(xi, dtype=np.float64)
+        c, s = np.cos(xi), np.sin(xi)
+        prim = np.empty((5, xi.size))
+        B = np.empty((3, xi.size))
+        prim[0] = self.rho
+        prim[4] = self.p
+        for d in range(3):
+            prim[1 + d] = -self.vA * self.eta * (self.Y[d] * c + self.Z[d] * s)
+            B[d] = self.B0 * self.X[d] + self.eta * self.B0 * (self.Y[d] * c + self.Z[d] * s)
+        return prim, B
+
+
+# ---------------------------------------------------------------------------
+# Random single-cell states (for the inversion tests)
+# ---------------------------------------------------------------------------
+
+def random_states(n, seed, lorentz_max=10.0, sigma_max=100.0, sigma_min=1e-3,
+                  theta_min=1e-2, theta_max=1e2):
+    """n random physical states: rho log-uniform in [0.1, 10], temperature p/rho
+    log-uniform in [theta_min, theta_max], Lorentz factor log-uniform in
+    [1, lorentz_max], magnetisation sigma = B^2/rho log-uniform in
+    [sigma_min, sigma_max], isotropic random directions for v and B.
+    Returns prim[5, n] (rho, vx, vy, vz, p) and B[3, n]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def logu(lo, hi, size):
+        return np.exp(rng.uniform(math.log(lo), math.log(hi), size))
+
+    def unit(size):
+        v = rng.normal(size=(3, size))
+        return v / np.linalg.norm(v, axis=0)
+
+    rho = logu(0.1, 10.0, n)
+    p = rho * logu(theta_min, theta_max, n)
+    lor = logu(1.0, lorentz_max, n)
+    vmag = np.sqrt(1.0 - 1.0 / lor ** 2)
+    v = unit(n) * vmag
+    bmag = np.sqrt(rho * logu(sigma_min, sigma_max, n))
+    B = unit(n) * bmag
+    prim = np.vstack([rho[None], v, p[None]])
+    return prim, B
+
+
+def random_smooth_fields(nx, ny, nz, seed, amp=0.3, kmax=2, L=(1.0, 1.0, 1.0),
+                         rho0=1.0, p0=1.0, B0=(0.7, 0.4, 0.3)):
+    """A smooth random periodic state for parity tests: a few Fourier modes
+    (|m| <= kmax) of random phase on rho, v, p at cell centres and on the edge
+    vector potential.  Returns prim5[5], bface background [3] (uniform B0) and
+    apot[3]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    modes = [(a, b, c) for a in range(-kmax, kmax + 1) for b in range(-kmax, kmax + 1)
+             for c in range(-kmax, kmax + 1) if 0 < a * a + b * b + c * c <= kmax * kmax]
+
+    def field(off, scale, nmodes=6):
+        x, y, z = _coords(nx, ny, nz, *L, off)
+        f = np.zeros((nz, ny, nx))
+        for q in rng.choice(len(modes), size=nmodes, replace=False):
+            m = modes[q]
+            ph = rng.uniform(0, 2 * math.pi)
+            a = rng.uniform(-1, 1) * scale
+            k = 2 * math.pi * np.array(m) / np.array(L)
+            f = f + a * np.cos(k[0] * x + k[1] * y + k[2] * z + ph)
+        return f / nmodes
+
+    prim = np.empty((5, nz, ny, nx))
+    prim[0] = rho0 * (1.0 + 0.5 * amp * field((0.5, 0.5, 0.5), 1.0))
+    for d in range(3):
+        prim[1 + d] = amp * field((0.5, 0.5, 0.5), 1.0)
+    prim[4] = p0 * (1.0 + 0.5 * amp * field((0.5, 0.5, 0.5), 1.0))
+    bg = np.empty((3, nz, ny, nx))
+    for d in range(3):
+        bg[d] = B0[d]
+    offs = [(0.5, 1.0, 1.0), (1.0, 0.5, 1.0), (1.0, 1.0, 0.5)]
+    apot = np.empty((3, nz, ny, nx))
+    for c in range(3):
+        apot[c] = amp * field(offs[c], 1.0) / (2 * math.pi)
+    return prim, bg, apot

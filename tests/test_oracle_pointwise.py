@@ -1,0 +1,389 @@
+"""Pins of the oracle's point-wise functions against closed forms, limits, identities
+and the values the paper prints (tests/golden/paper_printed_values.txt)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2401_03008_gb300 import workloads as wl
+
+GAM = 4.0 / 3.0
+
+
+def golden(golden_dir):
+    vals = {}
+    with open(os.path.join(golden_dir, "paper_printed_values.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if "=" in line:
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
+    return vals
+
+
+# --------------------------------------------------------------------------
+# the test problem itself (generator side)
+# --------------------------------------------------------------------------
+
+def test_alfven_speed_closed_form_and_limits():
+    # rho = p = B0 = eta = 1, gam = 4/3: rho h = 5, the quadratic gives (3 - sqrt 5)/2
+    assert wl.alfven_speed() == pytest.approx((3 - math.sqrt(5)) / 2, rel=1e-15)
+    # small amplitude: v_A^2 -> B0^2 / (rho h + B0^2) (Sec. 4)
+    va = wl.alfven_speed(rho=1.0, p=1.0, B0=1.0, eta=1e-6)
+    assert va ** 2 == pytest.approx(1.0 / 6.0, rel=1e-10)
+    # Newtonian limit p << rho, B0^2 << rho: v_A^2 -> B0^2 / rho
+    va = wl.alfven_speed(rho=1.0, p=1e-12, B0=1e-4, eta=1e-6)
+    assert va ** 2 == pytest.approx(1e-8, rel=1e-6)
+
+
+def test_golden_cpa_parameters(golden_dir):
+    g = golden(golden_dir)
+    cpa = wl.CPA(8, 8, 8, m=(1, 1, 1), rho=g["cpa.rho"], p=g["cpa.p"], B0=g["cpa.B0"],
+                 eta=g["cpa.eta"], gam=g["cpa.gamma"])
+    assert cpa.kmag == pytest.approx(g["cpa.kmag"], rel=1e-14)
+    assert cpa.period == pytest.approx(1.0 / (math.sqrt(3.0) * cpa.vA), rel=1e-14)
+    X, Y, Z = cpa.X, cpa.Y, cpa.Z
+    assert np.allclose(np.cross(X, Y), Z) and np.isclose(np.dot(X, Y), 0.0)
+
+
+def test_golden_turbulence_speeds(golden_dir):
+    """The paper prints the sound and Alfven speeds of its turbulence background to
+    two digits; the oracle's fast-speed routine must reproduce them in the limits
+    where it reduces to each of them."""
+    g = golden(golden_dir)
+    rho0, p0, B0 = g["turb.rho0"], g["turb.p0"], g["turb.B0"]
+    assert B0 ** 2 / rho0 == g["turb.sigma0"] and 2 * p0 / B0 ** 2 == g["turb.beta0"]
+    # B = 0, at rest: the fast speed is the sound speed
+    lm, lp = orc.speeds([rho0, 0, 0, 0, p0], [0, 0, 0], GAM, 0)
+    # the paper's two-digit values are within 0.01 of the exact ones (0.5764 is
+    # printed as 0.57, 0.5759 as 0.58)
+    assert abs(lp - g["turb.cs"]) < 0.01 and lm == pytest.approx(-lp)
+    # very hot plasma: c_s -> 1/sqrt(3)
+    lm, lp = orc.speeds([1e-9, 0, 0, 0, 1.0], [0, 0, 0], GAM, 0)
+    assert lp == pytest.approx(g["turb.cs_limit"], rel=1e-8)
+    # magnetised, at rest: w^2 = cs^2 + ca^2 - cs^2 ca^2 with the printed cs, v_A
+    lm, lp = orc.speeds([rho0, 0, 0, 0, p0], [0, 0, B0], GAM, 0)
+    cs, ca = g["turb.cs"], g["turb.vA"]
+    assert lp ** 2 == pytest.approx(cs ** 2 + ca ** 2 - cs ** 2 * ca ** 2, abs=0.012)
+    # with p -> 0 (rho h -> rho0) the fast speed is the Alfven speed B/sqrt(rho h + B^2);
+    # keep p0's enthalpy through rho so that rho h = rho0 + 4 p0 as in the paper
+    lm, lp = orc.speeds([rho0 + 4 * p0, 0, 0, 0, 1e-12], [0, 0, B0], GAM, 0)
+    assert abs(lp - g["turb.vA"]) < 0.01
+    assert lp == pytest.approx(B0 / math.sqrt(rho0 + 4 * p0 + B0 ** 2), rel=1e-10)
+
+
+# --------------------------------------------------------------------------
+# prim -> cons, fluxes
+# --------------------------------------------------------------------------
+
+def test_prim2cons_special_cases():
+    rho, p = 1.7, 0.3
+    rhoh = rho + 4.0 * p
+    # at rest: D = rho, S = 0, U = rho + p/(gam-1) + B^2/2
+    B = np.array([0.3, -0.2, 0.5])
+    u = orc.prim2cons([rho, 0, 0, 0, p], B, GAM)
+    assert np.allclose(u, [rho, 0, 0, 0, rho + 3 * p + 0.5 * B @ B], rtol=1e-15, atol=1e-15)
+    # B = 0: D = rho G, S = rho h G^2 v, U = rho h G^2 - p
+    v = np.array([0.3, -0.4, 0.5])
+    G2 = 1.0 / (1 - v @ v)
+    u = orc.prim2cons([rho, *v, p], [0, 0, 0], GAM)
+    assert np.allclose(u, [rho * math.sqrt(G2), *(rhoh * G2 * v), rhoh * G2 - p], rtol=1e-14)
+    # v perpendicular to B: E x B = v B^2, so S = (W + B^2) v, U = W - p + (v^2 B^2 + B^2)/2
+    v = np.array([0.2, 0.1, 0.0])
+    B = np.array([0.0, 0.0, 1.3])
+    G2 = 1.0 / (1 - v @ v)
+    W = rhoh * G2
+    u = orc.prim2cons([rho, *v, p], B, GAM)
+    assert np.allclose(u[1:4], (W + B @ B) * v, rtol=1e-14)
+    assert u[4] == pytest.approx(W - p + 0.5 * ((v @ v) * (B @ B) + B @ B), rel=1e-14)
+
+
+def test_flux_static_state():
+    """At rest the only fluxes are the total stress p_tot delta - B B (Eq. 8)."""
+    rho, p = 2.0, 0.7
+    B = np.array([0.4, -1.1, 0.6])
+    for d in range(3):
+        f = orc.flux([rho, 0, 0, 0, p], B, GAM, d)
+        stress = -B * B[d]
+        stress[d] += p + 0.5 * B @ B
+        assert np.allclose(f[1:4], stress, rtol=1e-15, atol=1e-15)
+        assert f[0] == 0 and f[4] == 0 and np.all(f[5:] == 0)
+
+
+def test_momentum_flux_trace():
+    """The electromagnetic stress-energy tensor is traceless, so the trace of the
+    momentum flux is sum_d F_d(S_d) = rho h G^2 v^2 + 3 p + (E^2 + B^2)/2."""
+    prim, B = wl.random_states(200, seed=16)
+    for q in range(200):
+        v = prim[1:4, q]
+        E = -np.cross(v, B[:, q])
+        W = (prim[0, q] + 4 * prim[4, q]) / (1 - v @ v)
+        tr = sum(orc.flux(prim[:, q], B[:, q], GAM, d)[1 + d] for d in range(3))
+        want = W * (v @ v) + 3 * prim[4, q] + 0.5 * (E @ E + B[:, q] @ B[:, q])
+        assert tr == pytest.approx(want, rel=1e-13)
+        # the stress tensor is symmetric: F_d(S_i) = F_i(S_d)
+        F = np.array([orc.flux(prim[:, q], B[:, q], GAM, d)[1:4] for d in range(3)])
+        assert np.allclose(F, F.T, rtol=1e-14, atol=1e-14 * np.abs(F).max())
+
+
+def test_traveling_wave_identity():
+    """A profile U(X - v_A t) solves dU/dt + dF_X/dX = 0 iff F_X(U) - v_A U does not
+    depend on the phase.  This ties prim->cons, the physical flux, E = -v x B and
+    the Alfven speed of Sec. 4 together, with no derivative and no solver."""
+    for m in [(1, 0, 0), (1, 1, 1), (0, 2, 1)]:
+        cpa = wl.CPA(8, 8, 8, m=m)
+        xi = np.linspace(0, 2 * math.pi, 41)
+        prim, B = cpa.state_along(xi)
+        rows = []
+        for q in range(xi.size):
+            u = orc.prim2cons(prim[:, q], B[:, q], GAM)
+            state = np.concatenate([u, B[:, q]])
+            fX = sum(cpa.X[d] * orc.flux(prim[:, q], B[:, q], GAM, d) for d in range(3))
+            rows.append(fX - cpa.vA * state)
+        rows = np.array(rows)
+        assert np.max(np.abs(rows - rows.mean(axis=0))) < 2e-14
+        # sensitivity: the small-amplitude speed is wrong for eta = 1 and must fail
+        va_lin = math.sqrt(1.0 / 6.0)
+        rows2 = []
+        for q in range(xi.size):
+            u = orc.prim2cons(prim[:, q], B[:, q], GAM)
+            fX = sum(cpa.X[d] * orc.flux(prim[:, q], B[:, q], GAM, d) for d in range(3))
+            rows2.append(fX - va_lin * np.concatenate([u, B[:, q]]))
+        rows2 = np.array(rows2)
+        assert np.max(np.abs(rows2 - rows2.mean(axis=0))) > 1e-3
+
+
+# --------------------------------------------------------------------------
+# C2P
+# --------------------------------------------------------------------------
+
+def _cons_of(prim, B):
+    n = prim.shape[1]
+    return np.array([orc.prim2cons(prim[:, q], B[:, q], GAM) for q in range(n)]).T
+
+
+def test_c2p_residual_vanishes_at_true_W():
+    """f(W) of the Newton scheme is zero at W = rho h G^2 of the state that made U."""
+    prim, B = wl.random_states(300, seed=11)
+    u = _cons_of(prim, B)
+    for q in range(prim.shape[1]):
+        v2 = prim[1:4, q] @ prim[1:4, q]
+        W = (prim[0, q] + 4.0 * prim[4, q]) / (1 - v2)
+        f, df = orc.c2p_fdf(u[:, q], B[:, q], GAM, W)
+        assert abs(f) <= 1e-13 * max(u[4, q], 1.0), (q, f)
+        assert df > 0
+
+
+def test_c2p_derivative_matches_finite_difference():
+    prim, B = wl.random_states(100, seed=12)
+    u = _cons_of(prim, B)
+    for q in range(prim.shape[1]):
+        v2 = prim[1:4, q] @ prim[1:4, q]
+        W = (prim[0, q] + 4.0 * prim[4, q]) / (1 - v2) * 1.01
+        h = 1e-5 * W
+        fp, _ = orc.c2p_fdf(u[:, q], B[:, q], GAM, W + h)
+        fm, _ = orc.c2p_fdf(u[:, q], B[:, q], GAM, W - h)
+        _, df = orc.c2p_fdf(u[:, q], B[:, q], GAM, W)
+        assert df == pytest.approx((fp - fm) / (2 * h), rel=1e-6)
+
+
+@pytest.mark.parametrize("guess", ["cold", "exact"])
+def test_c2p_round_trip(guess):
+    """prim -> cons -> prim on random states (Lorentz factor <= 10, sigma <= 100)."""
+    prim, B = wl.random_states(3000, seed=13)
+    u = _cons_of(prim, B)
+    v2 = np.sum(prim[1:4] ** 2, axis=0)
+    Wtrue = (prim[0] + 4.0 * prim[4]) / (1 - v2)
+    W0 = u[4].copy() if guess == "cold" else Wtrue
+    out, W, it, fails = orc.c2p_batch(u, B, W0, GAM)
+    assert fails == 0
+    assert np.max(np.abs(W - Wtrue) / Wtrue) < 1e-13
+    lor = 1 / np.sqrt(1 - v2)
+    assert np.max(np.abs(out[0] - prim[0]) / prim[0]) < 1e-12
+    # velocity error relative to the speed of light (|v| <= 1)
+    assert np.max(np.abs(out[1:4] - prim[1:4])) < 1e-13
+    # p is recovered by a difference of O(rho h G^2) terms: relative to rho h
+    rhoh = prim[0] + 4 * prim[4]
+    assert np.max(np.abs(out[4] - prim[4]) / rhoh * 1.0 / lor ** 0) < 1e-12
+    if guess == "exact":
+        assert np.all(it <= 3)
+
+
+def test_c2p_reports_unphysical_state():
+    # total energy below the rest mass: no physical inversion exists
+    u = np.array([1.0, 0.0, 0.0, 0.0, 0.5])
+    prim, W, it, bad = orc.c2p(u, [0.0, 0.0, 0.0], GAM, 1.0, maxit=50)
+    assert bad == 1
+
+
+# --------------------------------------------------------------------------
+# speeds and HLL
+# --------------------------------------------------------------------------
+
+def test_speeds_hydro_velocity_addition():
+    """B = 0 and v along d: lambda = (v +- cs) / (1 +- v cs) (relativistic addition)."""
+    rho, p = 1.3, 0.9
+    cs = math.sqrt(GAM * p / (rho + 4 * p))
+    for v in [-0.7, -0.1, 0.0, 0.4, 0.95]:
+        for d in range(3):
+            vel = [0.0, 0.0, 0.0]
+            vel[d] = v
+            lm, lp = orc.speeds([rho, *vel, p], [0, 0, 0], GAM, d)
+            assert lp == pytest.approx((v + cs) / (1 + v * cs), rel=1e-14, abs=1e-15)
+            assert lm == pytest.approx((v - cs) / (1 - v * cs), rel=1e-14, abs=1e-15)
+
+
+def test_speeds_strong_field_limit_and_symmetry():
+    lm, lp = orc.speeds([1.0, 0.3, -0.2, 0.1, 1.0], [1e7, 0, 0], GAM, 0)
+    assert lp == pytest.approx(1.0, abs=1e-9) and lm == pytest.approx(-1.0, abs=1e-9)
+    prim, B = wl.random_states(50, seed=14)
+    for q in range(50):
+        pr = prim[:, q].copy()
+        lm, lp = orc.speeds(pr, B[:, q], GAM, 1)
+        pr[1:4] *= -1
+        lm2, lp2 = orc.speeds(pr, B[:, q], GAM, 1)
+        assert lm2 == pytest.approx(-lp, rel=1e-12, abs=1e-14)
+        assert -1 < lm < lp < 1
+
+
+def test_hll_consistency():
+    """F_hll(U, U) = F(U) for every component and direction."""
+    prim, B = wl.random_states(100, seed=15)
+    for q in range(100):
+        for d in range(3):
+            fh, ap, am = orc.hll(prim[:, q], B[:, q], prim[:, q], B[:, q], GAM, d)
+            f = orc.flux(prim[:, q], B[:, q], GAM, d)
+            assert np.allclose(fh, f, rtol=1e-13, atol=1e-13 * np.max(np.abs(f)))
+            lm, lp = orc.speeds(prim[:, q], B[:, q], GAM, d)
+            assert ap == max(0.0, lp) and am == max(0.0, -lm)
+
+
+def test_hll_upwind_when_supersonic():
+    """When every wave moves in one direction HLL is the upwind flux: F_L for flow
+    faster than the fastest wave to the right, F_R for the mirror case."""
+    rng = np.random.default_rng(6)
+    for _ in range(30):
+        for d in range(3):
+            sgn = rng.choice([-1.0, 1.0])
+            pL = np.array([rng.uniform(0.5, 2), 0, 0, 0, rng.uniform(1e-3, 1e-2)])
+            pR = np.array([rng.uniform(0.5, 2), 0, 0, 0, rng.uniform(1e-3, 1e-2)])
+            pL[1 + d] = pR[1 + d] = 0.99 * sgn
+            BL = rng.uniform(-0.05, 0.05, 3)
+            BR = rng.uniform(-0.05, 0.05, 3)
+            fh, ap, am = orc.hll(pL, BL, pR, BR, GAM, d)
+            up = (pL, BL) if sgn > 0 else (pR, BR)
+            assert (am == 0.0) if sgn > 0 else (ap == 0.0)
+            assert np.allclose(fh, orc.flux(*up, GAM, d), rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# REC, INT, DER stencils
+# --------------------------------------------------------------------------
+
+def test_mp5_exact_on_quartics_when_smooth():
+    rng = np.random.default_rng(0)
+    x = np.arange(-2, 3, dtype=np.float64)
+    for deg in range(5):
+        for _ in range(20):
+            c = np.zeros(deg + 1)
+            c[0] = rng.uniform(-1, 1)
+            if deg >= 1:
+                c[1] = 1.0
+            if deg >= 2:
+                c[2:] = rng.uniform(-0.04, 0.04, deg - 1)
+            poly = np.polynomial.Polynomial(c)
+            assert orc.mp5(poly(x)) == pytest.approx(poly(0.5), abs=1e-14)
+    # not exact for a quintic: the interpolant is fifth order, not sixth
+    poly = np.polynomial.Polynomial([0, 1, 0, 0, 0, 0.01])
+    assert abs(orc.mp5(poly(x)) - poly(0.5)) > 1e-6
+
+
+def test_mp5_monotone_at_jumps():
+    for s in [(0, 0, 0, 1, 1), (0, 0, 1, 1, 1), (1, 1, 1, 0, 0), (0, 0, 1, 0, 0), (0, 1, 0, 1, 0)]:
+        v = orc.mp5(s)
+        lo, hi = min(s[2], s[3]), max(s[2], s[3])
+        if s[1] <= s[2] <= s[3] or s[1] >= s[2] >= s[3]:
+            assert lo - 1e-15 <= v <= hi + 1e-15, (s, v)
+    # a monotone step must not overshoot
+    assert orc.mp5([0, 0, 0, 1, 1]) <= 1.0 and orc.mp5([0, 0, 0, 1, 1]) >= 0.0
+
+
+def test_int_exact_on_polynomials():
+    xs = np.array([-1.5, -0.5, 0.5, 1.5])
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        p3 = np.polynomial.Polynomial(rng.uniform(-1, 1, 4))
+        assert orc.interp(p3(xs), 1) == pytest.approx(p3(0.0), abs=1e-14)
+        p1 = np.polynomial.Polynomial(rng.uniform(-1, 1, 2))
+        assert orc.interp(p1(xs), 0) == pytest.approx(p1(0.0), abs=1e-15)
+    p4 = np.polynomial.Polynomial([0, 0, 0, 0, 1.0])
+    assert abs(orc.interp(p4(xs), 1) - p4(0.0)) > 1e-3
+
+
+def test_der_exact_on_polynomials():
+    h = 0.1
+    xs = (np.arange(6) - 2.5) * h
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        p6 = np.polynomial.Polynomial(rng.uniform(-1, 1, 7))
+        assert orc.der(p6(xs), h, 1) == pytest.approx(p6.deriv()(0.0), abs=1e-10)
+        p2 = np.polynomial.Polynomial(rng.uniform(-1, 1, 3))
+        assert orc.der(p2(xs), h, 0) == pytest.approx(p2.deriv()(0.0), abs=1e-12)
+    p7 = np.polynomial.Polynomial([0, 0, 0, 0, 0, 0, 0, 1.0])
+    assert abs(orc.der(p7(xs), h, 1) - p7.deriv()(0.0)) > 1e-9
+
+
+# --------------------------------------------------------------------------
+# UCT
+# --------------------------------------------------------------------------
+
+def test_uct_uniform_state():
+    """For a uniform state the edge field is -(v x B) along the edge."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        v = rng.uniform(-0.5, 0.5, 3)
+        B = rng.uniform(-1, 1, 3)
+        sp = rng.uniform(0.1, 1, 4)
+        for c in range(3):
+            a, b = (c + 1) % 3, (c + 2) % 3
+            va = np.full((2, 2), v[a])
+            vb = np.full((2, 2), v[b])
+            E = orc.uct_point(va, vb, [B[a]] * 2, [B[b]] * 2, *sp)
+            assert E == pytest.approx(-np.cross(v, B)[c], abs=1e-15)
+
+
+def test_uct_reduces_to_hll_without_transverse_variation():
+    """No variation along b: the edge field is minus the HLL flux of B_b along a."""
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        vaL, vaR, vbL, vbR = rng.uniform(-0.5, 0.5, 4)
+        BbL, BbR, Ba = rng.uniform(-1, 1, 3)
+        apa, ama, apb, amb = rng.uniform(0.1, 1, 4)
+        va = np.array([[vaL, vaL], [vaR, vaR]])
+        vb = np.array([[vbL, vbL], [vbR, vbR]])
+        E = orc.uct_point(va, vb, [Ba, Ba], [BbL, BbR], apa, ama, apb, amb)
+        # flux of B_b along a: v_a B_b - v_b B_a = -E_c
+        FL = vaL * BbL - vbL * Ba
+        FR = vaR * BbR - vbR * Ba
+        F = (apa * FL + ama * FR - apa * ama * (BbR - BbL)) / (apa + ama)
+        assert E == pytest.approx(-F, abs=1e-14)
+
+
+def test_uct_reduces_to_hll_along_b():
+    """No variation along a: the edge field is plus the HLL flux of B_a along b."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        vaL, vaR, vbL, vbR = rng.uniform(-0.5, 0.5, 4)
+        BaL, BaR, Bb = rng.uniform(-1, 1, 3)
+        apa, ama, apb, amb = rng.uniform(0.1, 1, 4)
+        # index [s][t]: s = a-side (no variation), t = b-side
+        va = np.array([[vaL, vaR], [vaL, vaR]])
+        vb = np.array([[vbL, vbR], [vbL, vbR]])
+        E = orc.uct_point(va, vb, [BaL, BaR], [Bb, Bb], apa, ama, apb, amb)
+        # flux of B_a along b: v_b B_a - v_a B_b = +E_c
+        FL = vbL * BaL - vaL * Bb
+        FR = vbR * BaR - vaR * Bb
+        F = (apb * FL + amb * FR - apb * amb * (BaR - BaL)) / (apb + amb)
+        assert E == pytest.approx(F, abs=1e-14)
