@@ -1,0 +1,325 @@
+"""Benchmark: cell-updates per second of the SSP-RK3 step on one GB300.
+
+Workload (default): the circularly polarised relativistic Alfven wave with k along
+(1,1,1) on a periodic 256^3 grid, FP64, UCT and high-order INT/DER on, MP5,
+CFL 0.4.  One "step" is one full SSP-RK3 step (three substeps of the whole
+right-hand side) over all cells; value = cells * steps / time.
+
+The state (about 8 GB) is far larger than the 129 MB L2, so no flush is needed
+between timed steps.  Prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per GB300 (SSP-RK3 step, FP64)"
+UNIT = "cell-updates/s"
+
+# Algorithmic per-unit costs of each kernel kind: one unit is one cell, face or edge
+# of the launch.  Bytes: each array element read or written once (stencil
+# neighbours come from cache).  FLOPs: FP64 (or FP32 in the mixed path)
+# floating-point operations the algorithm performs per unit, an FMA counted as 2,
+# as counted by ncu (sass thread instructions, FP64 add/mul/fma) on the 256^3
+# workload; see the design doc.
+R64, R32 = 8, 4
+
+
+def bytes_per_unit(kind, r):
+    return {
+        "int_c2p": 5 * 8 + 3 * 8 + 8 + 8 * r + 8,
+        "flux_x": 8 * r + 8 + 5 * r + 6 * r, "flux_y": 8 * r + 8 + 5 * r + 6 * r,
+        "flux_z": 8 * r + 8 + 5 * r + 6 * r,
+        "der_x": 5 * r + 5 * r, "der_y": 5 * r + 10 * r, "der_z": 5 * r + 10 * r,
+        "uct_x": 8 * r + 16 + r, "uct_y": 8 * r + 16 + r, "uct_z": 8 * r + 16 + r,
+        "rk_curl": 5 * r + 3 * r + 3 * 64,
+    }.get(kind)
+
+
+FLOPS_PER_UNIT = {}  # filled from the ncu counts (profiles/), kernel -> flops per unit
+
+
+def load_flops_table():
+    p = os.path.join(ROOT, "profiles", "flops_per_unit.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.samples = []
+        self.proc = None
+        self.device = device
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_state(n, wave):
+    from paper_2401_03008_gb300 import workloads as wl
+    m = {"oblique": (1, 1, 1), "x": (1, 0, 0)}[wave]
+    c = wl.CPA(n, n, n, m=m)
+    return c, (c.prim5(), c.bface_background(), c.apot())
+
+
+def run_reference(args, world, rank):
+    """The oracle (plain FP64 C, all host cores) on a bounded sample of the same
+    workload: the same wave on a smaller grid, one SSP-RK3 step per timed step."""
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    nthreads = os.cpu_count() or 1
+    ns = args.ref_n
+    c, st = workload_state(ns, args.wave)
+    g = orc.Grid(ns, ns, ns, nthreads=nthreads)
+    g.set_state(*st)
+    g.step(args.warmup)
+    t0 = time.perf_counter()
+    g.step(args.steps)
+    el = time.perf_counter() - t0
+    value = ns ** 3 * args.steps / el
+    sample = "%d^3 grid, same wave, %d SSP-RK3 steps (oracle)" % (ns, args.steps)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(args),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def workload_config(args):
+    return {"workload": "relativistic circularly polarised Alfven wave, k along %s, "
+                        "%d^3 periodic, UCT + HO on, MP5, CFL 0.4, SSP-RK3"
+                        % ({"oblique": "(1,1,1)", "x": "x"}[args.wave], args.n),
+            "cells": args.n ** 3, "precision": args.precision, "wave": args.wave,
+            "l2_flush": "not needed: state of ~%.1f GB >> 129 MB L2" %
+                        (args.n ** 3 * (472 if args.precision == "fp64" else 336) / 1e9),
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def cpu_baseline(args):
+    from oracle import oracle as orc
+    nthreads = os.cpu_count() or 1
+    ns, steps = args.cpu_n, args.cpu_steps
+    c, st = workload_state(ns, args.wave)
+    g = orc.Grid(ns, ns, ns, nthreads=nthreads)
+    g.set_state(*st)
+    t0 = time.perf_counter()
+    g.step(steps)
+    el = time.perf_counter() - t0
+    return {"value": ns ** 3 * steps / el, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": "%d^3 grid of the same wave, %d SSP-RK3 steps, %.1f s" % (ns, steps, el)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--wave", default="oblique", choices=["oblique", "x"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--ref-n", type=int, default=48)
+    ap.add_argument("--cpu-n", type=int, default=64)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--prof-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_2401_03008_gb300 import echo
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    n = args.n
+    c, st = workload_state(n, args.wave)
+    stream = torch.cuda.current_stream()
+    s = echo.Solver(n, n, n, precision=args.precision, device=local,
+                    stream=stream.cuda_stream)
+    s.set_state(*st)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = s.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    done, t = s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = s.launches - l0
+    clocks = clk.stop()
+    assert done == args.steps
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * n ** 3 * args.steps / (ms * 1e-3)
+    diag = s.diagnostics()
+
+    # per-kernel device time over a profiled pass (events on the launching stream)
+    s.profile(True)
+    s.profile_read(reset=True)
+    s.step(args.prof_steps)
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    tot = sum(v[1] for v in prof.values())
+    top = max(prof, key=lambda k: prof[k][1])
+    cnt, kms = prof[top]
+    per_launch_s = kms / cnt * 1e-3
+
+    # roofline of the dominant kernel
+    import json as _json
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fp = "fp64" if args.precision == "fp64" else "fp32"
+    alu_peak = s.probe_fma_peak("fp64" if top == "int_c2p" or fp == "fp64" else "fp32")
+    r = R64 if args.precision == "fp64" else R32
+    units = n ** 3
+    flops_tab = load_flops_table().get(args.precision, {})
+    fpu = flops_tab.get(top)
+    bpu = bytes_per_unit(top, r)
+    t_alu = fpu * units / alu_peak if fpu else 0.0
+    t_hbm = bpu * units / (hbm_peak * 1e9) if bpu else 0.0
+    if fpu and t_alu >= t_hbm:
+        achieved = fpu * units / per_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / (alu_peak / 1e12),
+                "peak_source": "measured FMA-chain probe (%s vector)" %
+                               ("FP64" if fp == "fp64" or top == "int_c2p" else "FP32")}
+    else:
+        achieved = bpu * units / per_launch_s / 1e9 if bpu else None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak if achieved else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+    roof.update({"kernel": top, "traffic": None, "launch_ms": per_launch_s * 1e3,
+                 "share": kms / tot})
+    tr = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
+    if os.path.exists(tr):
+        tt = _json.load(open(tr)).get(args.precision, {}).get(top)
+        if tt:
+            roof["traffic"] = tt * (units / 256 ** 3)
+
+    # end to end through the C ABI with host buffers: every step uploads the state
+    # from pinned host memory, advances one step and reads the state back
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        cons, bf, w = pin((5, n, n, n)), pin((3, n, n, n)), pin((n, n, n))
+        _, _, _, t0s, st0 = s.get_state(cons, bf, w)
+        ke = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        q0 = time.perf_counter()
+        for _ in range(ke):
+            s.set_conserved(cons, bf, w, t0s, st0)
+            s.step(1)
+            _, _, _, t0s, st0 = s.get_state(cons, bf, w)
+        el = time.perf_counter() - q0
+        by = (cons.nbytes + bf.nbytes + w.nbytes)
+        e2e = {"value": world * n ** 3 * ke / el, "unit": UNIT, "h2d_bytes_per_step": by,
+               "d2h_bytes_per_step": by, "steps": ke}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic (analytic Alfven wave)", "config": workload_config(args),
+           "roofline": roof, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
+           "kernel_ms_per_step": {k: v[1] / args.prof_steps for k, v in sorted(prof.items())},
+           "diag": {"t": diag["t"], "divb_max": diag["divb_max"],
+                    "newton_it_mean": diag["newton_it_mean"],
+                    "c2p_failures": diag["c2p_failures"]}}
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out))
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * echo.h -- C ABI of libecho: the per-timestep right-hand-side update of the ECHO
+ * special-relativistic MHD scheme (arXiv 2401.03008) on a periodic 3-D Cartesian
+ * grid, computed by hand-written CUDA kernels for sm_103a (NVIDIA GB300).
+ *
+ * What one step computes (Sec. 3, the five numbered steps of one Runge-Kutta
+ * substep, applied to the flat-space ideal-MHD system of Sec. 2, Eq. 8):
+ *   1. INT of the staggered field to cell centres and the Newton inversion of
+ *      conserved to primitive variables (C2P);
+ *   2. MP5 reconstruction of primitives at every interface, physical fluxes,
+ *      fast speeds and the HLL flux;
+ *   3. DER of the numerical fluxes into the right-hand side (Eq. 9);
+ *   4. UCT edge electric fields and their curl (Eq. 10), which keeps the discrete
+ *      div B at round-off;
+ *   5. the SSP-RK3 stage combination; the timestep from the largest fast speed,
+ *      once per full step.
+ *
+ * Conventions shared by every entry point
+ *   - Grid arrays are float64, structure of arrays, [var][nz][ny][nx] with x
+ *     fastest, periodic, no ghost cells.  Cell (i,j,k) is centred at
+ *     ((i+1/2)hx, (j+1/2)hy, (k+1/2)hz) with h = L/n per direction.
+ *   - Face array d, index (i,j,k): the face half a cell above the centre of cell
+ *     (i,j,k) along d (Bx at (i+1/2, j, k), ...).  Edge array c, index (i,j,k): the
+ *     edge half a cell above the centre along both directions other than c
+ *     (Ax at (i, j+1/2, k+1/2), ...).
+ *   - ptr_kind: ECHO_PTR_HOST for host memory (copied synchronously), or
+ *     ECHO_PTR_DEVICE for device memory of the context's device (for example a
+ *     torch tensor's data_ptr()); device pointers must stay valid until the call
+ *     returns.  Input buffers are caller-owned and only read; output buffers are
+ *     caller-allocated and fully overwritten.
+ *   - Every call returns an echo_status.  Nothing aborts, traps or prints.  The
+ *     text of the last error of a context is available from echo_last_error().
+ *   - A context is used by one host thread at a time.  There is no global state.
+ */
+#ifndef ECHO_H
+#define ECHO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct echo_ctx echo_ctx; /* opaque; created and owned by the library */
+
+typedef enum {
+    ECHO_OK = 0,
+    ECHO_ERR_ARG = -1,       /* invalid argument or configuration */
+    ECHO_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+    ECHO_ERR_OOM = -3,       /* device allocation failed */
+    ECHO_ERR_C2P = -4,       /* Newton inversion failed somewhere; state rolled back */
+    ECHO_ERR_NONFINITE = -5, /* non-finite value in the state; state rolled back */
+    ECHO_ERR_STATE = -6      /* call out of order (for example step before set_state) */
+} echo_status;
+
+enum { ECHO_PTR_HOST = 0, ECHO_PTR_DEVICE = 1 };
+enum { ECHO_REC_MP5 = 0 };
+/* ECHO_FP64: every step in double precision.  ECHO_MIXED: reconstruction, fluxes,
+ * HLL, DER and the UCT fields in single precision; the inversion (Lorentz factor and
+ * pressure recovery included) and the Runge-Kutta accumulation of the conserved
+ * state in double precision. */
+enum { ECHO_FP64 = 0, ECHO_MIXED = 1 };
+/* Newton starting guess: W of the previous call at the same cell, W0 = U, or the
+ * small learned network loaded with echo_mlp_load (falls back to the previous W
+ * where its guess is unusable). */
+enum { ECHO_GUESS_PREV = 0, ECHO_GUESS_COLD = 1, ECHO_GUESS_MLP = 2 };
+
+typedef struct {
+    int nx, ny, nz;     /* cells per direction, periodic; each >= 1 */
+    double lx, ly, lz;  /* box lengths (> 0) */
+    double gamma_ad;    /* adiabatic index of the ideal-gas law (Sec. 2, Eq. 7) */
+    double cfl;         /* dt = cfl * min(h) / max fast speed (Sec. 3 step 5) */
+    int uct;            /* must be 1: staggered field evolved by UCT (Sec. 3) */
+    int ho;             /* 1: fourth-order INT and sixth-order DER; 0: two-point forms */
+    int rec;            /* ECHO_REC_MP5 */
+    int precision;      /* ECHO_FP64 or ECHO_MIXED */
+    int c2p_guess;      /* ECHO_GUESS_* */
+    double c2p_tol;     /* Newton stop |dW| <= tol W, then one polishing step */
+    int c2p_maxit;      /* Newton iteration cap (a cell past it is a failure) */
+    int device;         /* CUDA device ordinal */
+    void *stream;       /* cudaStream_t to launch on; NULL: the library makes one */
+} echo_config;
+
+/* Fill *cfg with defaults: 32^3 unit box, gamma 4/3, cfl 0.4, uct 1, ho 1, MP5,
+ * FP64, previous-W guess, tol 1e-12, maxit 100, device 0, own stream. */
+echo_status echo_config_default(echo_config *cfg);
+
+/* Validate cfg, select its device, allocate the device state (library-owned) and
+ * return a context in *out.  ECHO_ERR_ARG for an invalid configuration,
+ * ECHO_ERR_OOM when the device memory does not fit. */
+echo_status echo_create(const echo_config *cfg, echo_ctx **out);
+
+/* Free everything the context owns.  NULL is accepted. */
+echo_status echo_destroy(echo_ctx *ctx);
+
+/* Initial data (Sec. 4 and Sec. 5 set up the state from primitives and field).
+ *   prim  [5][nz][ny][nx]: rho, vx, vy, vz, p at cell centres (required);
+ *   bface [3][nz][ny][nx]: staggered field on faces (NULL: zero);
+ *   apot  [3][nz][ny][nx]: edge vector potential (NULL: none); its discrete curl,
+ *         with the same DER as the induction equation, is added to bface so that
+ *         the discrete div B is zero to round-off.
+ * The conserved variables follow from the definitions of Sec. 2 (D = rho G,
+ * S = rho h G^2 v + E x B, U = rho h G^2 - p + (E^2+B^2)/2, E = -v x B) with the
+ * cell-centred field from INT.  Resets t and the step count to 0.  ECHO_ERR_ARG for
+ * a NULL prim; ECHO_ERR_NONFINITE if the resulting state is not finite. */
+echo_status echo_set_state(echo_ctx *ctx, const double *prim, const double *bface,
+                           const double *apot, int ptr_kind);
+
+/* Advance by SSP-RK3 steps (Sec. 3, steps 1-5) until max_steps steps are done or
+ * t reaches t_end (the last step is shortened to land on t_end; pass
+ * INFINITY for no limit).  *steps_done and *t_now (either may be NULL) receive
+ * the steps taken and the time reached.  On ECHO_ERR_C2P or ECHO_ERR_NONFINITE the
+ * state, t and the step count are those at the start of the step that failed. */
+echo_status echo_step(echo_ctx *ctx, int max_steps, double t_end, int *steps_done,
+                      double *t_now);
+
+/* Evaluate the right-hand side L(U) of Eq. 9-10 once on the current state
+ * (Sec. 3 steps 1-4) without advancing it.
+ *   rhs_cons [5][nz][ny][nx]: dD/dt, dS/dt, dU/dt at cell centres;
+ *   rhs_face [3][nz][ny][nx]: dB/dt on faces;
+ *   amax: the largest HLL speed over all faces (may be NULL).
+ * The warm Newton guess is updated as a step would.  ECHO_ERR_C2P if the inversion
+ * failed somewhere (the outputs are then not meaningful). */
+echo_status echo_rhs(echo_ctx *ctx, double *rhs_cons, double *rhs_face, double *amax,
+                     int ptr_kind);
+
+/* Primitives for output: [8][nz][ny][nx] = rho, vx, vy, vz, p, Bx, By, Bz with the
+ * field at cell centres (INT) -- Sec. 3 step 1 applied to the current state. */
+echo_status echo_get_primitives(echo_ctx *ctx, double *out, int ptr_kind);
+
+/* Checkpoint: the conserved state cons5 [5][nz][ny][nx] (D, Sx, Sy, Sz, U), the
+ * staggered field bface [3][nz][ny][nx], the warm Newton guess w [nz][ny][nx],
+ * t and the step count.  Any output pointer may be NULL. */
+echo_status echo_get_state(echo_ctx *ctx, double *cons5, double *bface, double *w,
+                           double *t, long *step, int ptr_kind);
+
+/* Resume from a checkpoint written by echo_get_state (same layouts).  w may be NULL
+ * (the guess is then rebuilt by a cold inversion).  A resumed run is bit-identical
+ * to an uninterrupted one. */
+echo_status echo_set_conserved(echo_ctx *ctx, const double *cons5, const double *bface,
+                               const double *w, double t, long step, int ptr_kind);
+
+typedef struct {
+    double t, dt, amax;        /* time, last dt, largest fast speed of the last step */
+    double divb_max, divb_l2;  /* discrete div B (same DER as the curl), max |.| and RMS */
+    double tot[8];             /* sums of D, Sx, Sy, Sz, U and face Bx, By, Bz (compensated) */
+    double newton_it_mean;     /* Newton iterations per inversion since the last reset */
+    int newton_it_max;
+    long c2p_calls, c2p_fallbacks, c2p_failures;
+    long nonfinite;            /* non-finite values found in the state */
+    long step;
+} echo_diag;
+
+/* Diagnostics of the current state (Sec. 3: div B preserved by UCT; conservation of
+ * the periodic-box totals).  Reductions run in a fixed order, so the result is
+ * deterministic.  reset_counters != 0 clears the Newton counters afterwards. */
+echo_status echo_diagnostics(echo_ctx *ctx, echo_diag *out, int reset_counters);
+
+/* L1 norm per variable of (current primitives - ref) over the grid, divided by the
+ * cell count: ref [8][nz][ny][nx] in the layout of echo_get_primitives, out[8]. */
+echo_status echo_l1_error(echo_ctx *ctx, const double *ref, int ptr_kind, double *out);
+
+/* Kernel timing for the benchmark: when enabled, every kernel launch of the
+ * context is bracketed by CUDA events on the context's stream.  echo_profile_read
+ * returns, for kernel kind k (0 <= k < ECHO_NKERNELS), its launch count and summed
+ * device time in ms, and its name in *name; the counters are then cleared when
+ * reset != 0.  echo_launches returns the number of kernels launched so far. */
+#define ECHO_NKERNELS 16
+echo_status echo_profile_enable(echo_ctx *ctx, int on);
+echo_status echo_profile_read(echo_ctx *ctx, int k, long *launches, double *ms,
+                              const char **name, int reset);
+long echo_launches(const echo_ctx *ctx);
+
+/* Measured vector peak (the roofline denominator of ALU-bound kernels): runs an
+ * independent-FMA-chain kernel on the context's device and returns FLOP/s in
+ * *flops (an FMA counts as 2).  precision: ECHO_FP64 or ECHO_MIXED (= FP32). */
+echo_status echo_probe_fma_peak(echo_ctx *ctx, int precision, double *flops);
+
+/* The context's stream (cudaStream_t) and device. */
+void *echo_stream(const echo_ctx *ctx);
+
+/* Text of the last error on ctx (a static string when ctx is NULL). */
+const char *echo_last_error(const echo_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ECHO_H */

@@ -1,0 +1,362 @@
+// Device-side building blocks of the ECHO RMHD right-hand side (arXiv 2401.03008).
+//
+// R is the precision of reconstruction, fluxes and constrained transport: double
+// for the FP64 path, float for the mixed path.  The inversion (C2P) and the
+// Runge-Kutta accumulation are always double.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace echo {
+
+// Grid description passed by value to every kernel.
+struct Grid {
+    int nx, ny, nz;
+    long n;            // cells (= faces per direction = edges per direction)
+    double h[3];       // cell sizes
+    double inv_h[3];
+    double hmin;
+    double gam;        // adiabatic index
+    int ho;            // high-order INT / DER
+};
+
+// Device-side scalars of the time loop and the health counters.
+struct DevScalars {
+    unsigned long long amax_bits;  // running max of a+, a- (non-negative double bits)
+    double amax_last;              // amax of the last step
+    double dt;                     // dt of the step in progress
+    double t;                      // time (advanced when dt is fixed)
+    double t_prev;                 // time at the start of the step in progress
+    double t_end;
+    double cfl;
+    unsigned long long it_sum;     // Newton iterations summed
+    unsigned long long c2p_calls;
+    unsigned int it_max;
+    unsigned int fails;            // failed inversions
+    unsigned int fallbacks;        // rejected learned guesses
+    unsigned int rec_fallbacks;    // interface states reset to first order
+    int halt;                      // bit 0: inversion failed, bit 1: t_end reached
+    int fail_stage;                // stage (1..3) of the first failure, 0 if none
+    long fail_step;                // step index of the first failure
+    long step;                     // steps completed
+};
+
+// Newton parameters.
+struct C2PParams {
+    double tol;
+    int maxit;
+    int guess;  // 0 previous W, 1 W0 = U, 2 learned guess array
+};
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    if ((unsigned)i < (unsigned)n) return i;
+    if (i < 0 && i + n >= 0) return i + n;
+    if (i >= n && i - n < n) return i - n;
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// linear index of cell (i,j,k) (already wrapped)
+__device__ __forceinline__ long lin(const Grid &g, int i, int j, int k)
+{
+    return ((long)k * g.ny + j) * g.nx + i;
+}
+
+// cell (i,j,k) moved by s along direction D, wrapped
+template <int D>
+__device__ __forceinline__ long shifted(const Grid &g, int i, int j, int k, int s)
+{
+    if (D == 0) i = wrapi(i + s, g.nx);
+    else if (D == 1) j = wrapi(j + s, g.ny);
+    else k = wrapi(k + s, g.nz);
+    return lin(g, i, j, k);
+}
+
+__device__ __forceinline__ long shifted_rt(const Grid &g, int i, int j, int k, int d, int s)
+{
+    if (d == 0) i = wrapi(i + s, g.nx);
+    else if (d == 1) j = wrapi(j + s, g.ny);
+    else k = wrapi(k + s, g.nz);
+    return lin(g, i, j, k);
+}
+
+__device__ __forceinline__ void coords(const Grid &g, long c, int &i, int &j, int &k)
+{
+    long q = c / g.nx;
+    i = (int)(c - q * g.nx);
+    k = (int)(q / g.ny);
+    j = (int)(q - (long)k * g.ny);
+}
+
+// ---------------------------------------------------------------------------
+// 1-D operators (REC, INT, DER of Sec. 3)
+// ---------------------------------------------------------------------------
+
+template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+
+template <typename R>
+__device__ __forceinline__ R minmod2(R a, R b)
+{
+    if (a > R(0) && b > R(0)) return rmin(a, b);
+    if (a < R(0) && b < R(0)) return rmax(a, b);
+    return R(0);
+}
+
+template <typename R>
+__device__ __forceinline__ R minmod4(R a, R b, R c, R d)
+{
+    if (a > R(0) && b > R(0) && c > R(0) && d > R(0)) return rmin(rmin(a, b), rmin(c, d));
+    if (a < R(0) && b < R(0) && c < R(0) && d < R(0)) return rmax(rmax(a, b), rmax(c, d));
+    return R(0);
+}
+
+// MP5 value at i+1/2 from (u_{i-2}, ..., u_{i+2}): fifth-order point-value
+// interpolant (3, -20, 90, 60, -5)/128 bounded by the monotonicity-preserving
+// limiter of Suresh & Huynh (alpha = 4, eps = 1e-10).
+template <typename R>
+__device__ __forceinline__ R mp5(R um2, R um1, R u0, R up1, R up2)
+{
+    const R alpha = R(4);
+    R uor = (R(3) * um2 - R(20) * um1 + R(90) * u0 + R(60) * up1 - R(5) * up2) * R(0.0078125);
+    R ump = u0 + minmod2(up1 - u0, alpha * (u0 - um1));
+    if ((uor - u0) * (uor - ump) <= R(1e-10)) return uor;
+    R djm1 = um2 - R(2) * um1 + u0;
+    R dj = um1 - R(2) * u0 + up1;
+    R djp1 = u0 - R(2) * up1 + up2;
+    R dm4p = minmod4(R(4) * dj - djp1, R(4) * djp1 - dj, dj, djp1);
+    R dm4m = minmod4(R(4) * dj - djm1, R(4) * djm1 - dj, dj, djm1);
+    R uul = u0 + alpha * (u0 - um1);
+    R uav = R(0.5) * (u0 + up1);
+    R umd = uav - R(0.5) * dm4p;
+    R ulc = u0 + R(0.5) * (u0 - um1) + R(4) / R(3) * dm4m;
+    R umin = rmax(rmin(rmin(u0, up1), umd), rmin(rmin(u0, uul), ulc));
+    R umax = rmin(rmax(rmax(u0, up1), umd), rmax(rmax(u0, uul), ulc));
+    return uor + minmod2(umin - uor, umax - uor);
+}
+
+// left state at i+1/2 from s[0..5] = u_{i-2..i+3}, and the mirrored right state
+template <typename R>
+__device__ __forceinline__ void mp5_lr(const R *s, R &L, R &Rr)
+{
+    L = mp5(s[0], s[1], s[2], s[3], s[4]);
+    Rr = mp5(s[5], s[4], s[3], s[2], s[1]);
+}
+
+// INT: staggered values at i-3/2, i-1/2, i+1/2, i+3/2 -> centre
+template <typename R>
+__device__ __forceinline__ R int_c(R a, R b, R c, R d, int ho)
+{
+    if (ho) return (-a + R(9) * b + R(9) * c - d) * R(0.0625);
+    return R(0.5) * (b + c);
+}
+
+// DER: derivative at a centre from staggered values s[0..5] at i-5/2..i+5/2;
+// high order corrects each staggered value by -d2/24 + 3 d4/640 first.
+template <typename R>
+__device__ __forceinline__ R der_c(const R *s, R inv_h, int ho)
+{
+    if (!ho) return (s[3] - s[2]) * inv_h;
+    R d2p = s[2] - R(2) * s[3] + s[4];
+    R d4p = s[1] - R(4) * s[2] + R(6) * s[3] - R(4) * s[4] + s[5];
+    R d2m = s[1] - R(2) * s[2] + s[3];
+    R d4m = s[0] - R(4) * s[1] + R(6) * s[2] - R(4) * s[3] + s[4];
+    R fp = s[3] - d2p / R(24) + R(3) * d4p / R(640);
+    R fm = s[2] - d2m / R(24) + R(3) * d4m / R(640);
+    return (fp - fm) * inv_h;
+}
+
+// ---------------------------------------------------------------------------
+// Point-wise physics (Sec. 2, flat space, ideal MHD, ideal gas)
+// ---------------------------------------------------------------------------
+
+// Conserved variables (D, S, U) and field, physical flux along D of all 8, and the
+// fast speeds lm <= lp along D, sharing the intermediate quantities.
+// s = (rho, vx, vy, vz, p, Bx, By, Bz).
+template <typename R, int D>
+__device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &lm, R &lp)
+{
+    const R rho = s[0], vx = s[1], vy = s[2], vz = s[3], pg = s[4];
+    const R bx = s[5], by = s[6], bz = s[7];
+    R v2 = vx * vx + vy * vy + vz * vz;
+    R omv2 = R(1) - v2;
+    R lor2 = R(1) / omv2;
+    R lor = sqrt(lor2);
+    R rhoh = rho + gfac * pg;
+    R w = rhoh * lor2;
+    // E = -v x B
+    R ex = -(vy * bz - vz * by);
+    R ey = -(vz * bx - vx * bz);
+    R ez = -(vx * by - vy * bx);
+    R e2 = ex * ex + ey * ey + ez * ez;
+    R b2 = bx * bx + by * by + bz * bz;
+    R D0 = rho * lor;
+    R Sx = w * vx + (ey * bz - ez * by);
+    R Sy = w * vy + (ez * bx - ex * bz);
+    R Sz = w * vz + (ex * by - ey * bx);
+    R ptot = pg + R(0.5) * (e2 + b2);
+    U[0] = D0;
+    U[1] = Sx;
+    U[2] = Sy;
+    U[3] = Sz;
+    U[4] = w - pg + R(0.5) * (e2 + b2);
+    U[5] = bx;
+    U[6] = by;
+    U[7] = bz;
+    const R vd = s[1 + D];
+    const R Ed = D == 0 ? ex : (D == 1 ? ey : ez);
+    const R Bd = s[5 + D];
+    F[0] = D0 * vd;
+    F[1] = w * vx * vd - ex * Ed - bx * Bd + (D == 0 ? ptot : R(0));
+    F[2] = w * vy * vd - ey * Ed - by * Bd + (D == 1 ? ptot : R(0));
+    F[3] = w * vz * vd - ez * Ed - bz * Bd + (D == 2 ? ptot : R(0));
+    F[4] = D == 0 ? Sx : (D == 1 ? Sy : Sz);
+    F[5] = vd * bx - vx * Bd;
+    F[6] = vd * by - vy * Bd;
+    F[7] = vd * bz - vz * Bd;
+    // approximate fast magnetosonic speeds
+    R cs2 = gam * pg / rhoh;
+    R vb = vx * bx + vy * by + vz * bz;
+    R bb2 = b2 * omv2 + vb * vb;
+    R ca2 = bb2 / (rhoh + bb2);
+    R w2 = cs2 + ca2 - cs2 * ca2;
+    R disc = w2 * omv2 * ((R(1) - v2 * w2) - vd * vd * (R(1) - w2));
+    disc = disc < R(0) ? R(0) : disc;
+    R sr = sqrt(disc);
+    R inv = R(1) / (R(1) - v2 * w2);
+    lp = (vd * (R(1) - w2) + sr) * inv;
+    lm = (vd * (R(1) - w2) - sr) * inv;
+}
+
+// ---------------------------------------------------------------------------
+// UCT four-state edge field; (a, b, c) cyclic, edge along c at (a+1/2, b+1/2).
+// va/vb[s][t]: velocity components a and b of the a-face state s (L/R) reconstructed
+// along b to side t; Ba[t]: B_a along b; Bb[s]: B_b along a.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const R Ba[2],
+                                       const R Bb[2], R apa, R ama, R apb, R amb)
+{
+    R sa = apa + ama, sb = apb + amb;
+    R e4 = R(0);
+    if (sa > R(0) && sb > R(0)) {
+        R wa[2] = {apa, ama}, wb[2] = {apb, amb};
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int t = 0; t < 2; t++)
+                e4 += wa[s] * wb[t] * (vb[s][t] * Ba[t] - va[s][t] * Bb[s]);
+        e4 = e4 / (sa * sb);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int t = 0; t < 2; t++)
+                e4 += R(0.25) * (vb[s][t] * Ba[t] - va[s][t] * Bb[s]);
+    }
+    R da = sa > R(0) ? apa * ama * (Bb[1] - Bb[0]) / sa : R(0);
+    R db = sb > R(0) ? apb * amb * (Ba[1] - Ba[0]) / sb : R(0);
+    return e4 + da - db;
+}
+
+// ---------------------------------------------------------------------------
+// C2P: Newton on W = rho h G^2 (always double)
+// ---------------------------------------------------------------------------
+struct C2PInv {
+    double D, S2, B2, SB, U, gm1g;
+};
+
+__device__ __forceinline__ double c2p_v2(const C2PInv &q, double W)
+{
+    double wb = W + q.B2;
+    return (q.S2 * W * W + q.SB * q.SB * (q.B2 + 2.0 * W)) / (W * W * wb * wb);
+}
+
+__device__ __forceinline__ bool c2p_ok(const C2PInv &q, double W)
+{
+    if (!(W > 0.0) || !isfinite(W)) return false;
+    double v2 = c2p_v2(q, W);
+    return isfinite(v2) && v2 < 1.0;
+}
+
+// Returns true on success.  prim = (rho, vx, vy, vz, p); B the cell-centred field.
+__device__ __forceinline__ bool c2p_newton(const double *u, const double *B, double gam,
+                                           double W0, double tol, int maxit, double *prim,
+                                           double &Wout, int &iters)
+{
+    C2PInv q;
+    q.D = u[0];
+    q.S2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+    q.B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    q.SB = u[1] * B[0] + u[2] * B[1] + u[3] * B[2];
+    q.U = u[4];
+    q.gm1g = (gam - 1.0) / gam;
+    double W = W0;
+    for (int k = 0; k < 64 && !c2p_ok(q, W); k++)
+        W = (W > 0.0 && isfinite(W)) ? 2.0 * W : fabs(q.U) + 1.0;
+    int it = 0;
+    bool conv = false, polish = false;
+    const double SB2 = q.SB * q.SB;
+    while (it < maxit) {
+        double iW = 1.0 / W;
+        double wb = W + q.B2;
+        double iwb = 1.0 / wb;
+        double v2 = (q.S2 * W * W + SB2 * (q.B2 + 2.0 * W)) * (iW * iW) * (iwb * iwb);
+        double sq1 = sqrt(1.0 - v2);
+        double p = q.gm1g * (W * (1.0 - v2) - q.D * sq1);
+        double dv2 = -2.0 * SB2 * (iW * iW * iW) * iwb - 2.0 * v2 * iwb;
+        double dp = q.gm1g * ((1.0 - v2) - W * dv2 + q.D * dv2 / (2.0 * sq1));
+        double f = W - p + 0.5 * (1.0 + v2) * q.B2 - 0.5 * SB2 * (iW * iW) - q.U;
+        double df = 1.0 - dp + 0.5 * q.B2 * dv2 + SB2 * (iW * iW * iW);
+        double dW = -f / df;
+        if (!isfinite(dW)) break;
+        double lam = 1.0, Wn = W + dW;
+        for (int k = 0; k < 60 && !c2p_ok(q, Wn); k++) {
+            lam *= 0.5;
+            Wn = W + lam * dW;
+        }
+        it++;
+        if (!c2p_ok(q, Wn)) break;
+        double step = fabs(Wn - W);
+        W = Wn;
+        if (polish) {
+            conv = true;
+            break;
+        }
+        if (step <= tol * W) polish = true;
+    }
+    iters = it;
+    Wout = W;
+    double v2 = c2p_v2(q, W);
+    double sq1 = sqrt(1.0 - v2);
+    double p = q.gm1g * (W * (1.0 - v2) - q.D * sq1);
+    double rho = q.D * sq1;
+    double wb = W + q.B2;
+    double iW = 1.0 / W;
+    for (int i = 0; i < 3; i++) prim[1 + i] = (u[1 + i] + q.SB * B[i] * iW) / wb;
+    prim[0] = rho;
+    prim[4] = p;
+    return conv && isfinite(p) && isfinite(rho) && p > 0.0 && rho > 0.0 && v2 < 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// warp / block reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace echo

@@ -1,0 +1,117 @@
+// Host-side context of libecho (shared by the API and the kernel translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/echo.h"
+#include "echo_device.cuh"
+
+namespace echo {
+
+// kernel kinds for launch counting and event timing
+enum Kind {
+    K_C2P = 0, K_FLUX_X, K_FLUX_Y, K_FLUX_Z, K_DER_X, K_DER_Y, K_DER_Z,
+    K_UCT_X, K_UCT_Y, K_UCT_Z, K_RK, K_DT, K_CURL, K_INIT, K_DIAG, K_MISC
+};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t e0, e1;
+};
+
+}  // namespace echo
+
+struct echo_ctx {
+    echo_config cfg;
+    echo::Grid g;
+    cudaStream_t stream;
+    bool own_stream;
+    int mixed;
+
+    // conserved state (double): U[5n], U0[5n], Bf[3n], Bf0[3n]; warm guess W[n]
+    double *U, *U0, *Bf, *Bf0, *W;
+    // work buffers in the reconstruction precision R (double or float)
+    void *prim;     // [8][n]  rho, vx, vy, vz, p, Bx, By, Bz at centres
+    void *flux;     // [5][n]  HLL flux of one direction
+    void *fdat[3];  // [6][n]  per direction: vL_d, vL_d+1, vR_d, vR_d+1, a+, a-
+    void *E;        // [3][n]  edge fields
+    void *rhs;      // [5][n]  cell right-hand side
+    echo::DevScalars *sc;   // device scalars
+    double *partials;       // reduction scratch of the diagnostics
+    double *dres;           // reduction results (device)
+    double *stage8;         // staging for host outputs [8][n] (allocated on demand)
+    float *mlp_w;           // learned-guess weights (device), or NULL
+    float *guess;           // learned guesses [n] (allocated on demand)
+
+    bool has_state;
+    long launches;
+    bool prof_on;
+    std::vector<echo::ProfRec> prof;
+    long prof_count[ECHO_NKERNELS];
+    double prof_ms[ECHO_NKERNELS];
+    char err[512];
+};
+
+namespace echo {
+
+// Launch helper: counts launches and, when profiling, brackets with events.
+template <typename Kernel, typename... Args>
+inline void launch(echo_ctx *c, int kind, Kernel k, dim3 grid, dim3 block, size_t smem,
+                   Args... args)
+{
+    ProfRec r;
+    if (c->prof_on) {
+        r.kind = kind;
+        cudaEventCreate(&r.e0);
+        cudaEventCreate(&r.e1);
+        cudaEventRecord(r.e0, c->stream);
+    }
+    k<<<grid, block, smem, c->stream>>>(args...);
+    if (c->prof_on) {
+        cudaEventRecord(r.e1, c->stream);
+        c->prof.push_back(r);
+    }
+    c->launches++;
+}
+
+inline unsigned nblocks(long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Number of blocks of the fixed-shape reductions (a multiple of the SM count of
+// the GB300, 152, so the partial sums have a fixed order).
+constexpr int DIAG_BLOCKS = 608;
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_Q = 24;  // quantities per block partial
+
+// Per-precision kernel launchers (one translation unit per precision).
+template <typename R>
+struct Path {
+    // INT + C2P into the work prims (R).  stage: 1..3 (0 for a one-off call);
+    // update_w: store the converged W as the next warm guess.
+    static void int_c2p(echo_ctx *c, int stage, long step, int update_w);
+    // sweeps + DER (steps 2-3), want_amax on the first stage of a step
+    static void sweeps(echo_ctx *c, int want_amax);
+    // UCT edge fields (step 4, first half)
+    static void uct(echo_ctx *c);
+    // RK stage with the curl of E (step 4, second half, and step 5)
+    static void rk(echo_ctx *c, int stage);
+    // curl of the work E into a face array: out = -curl E (as in dB/dt)
+    static void curl_out(echo_ctx *c, double *out);
+    // copy the work rhs (R) to a double array
+    static void rhs_out(echo_ctx *c, double *out);
+};
+
+// precision-independent launchers (FP64 translation unit)
+void launch_dt(echo_ctx *c);
+void launch_init(echo_ctx *c, const double *prim5);
+void launch_curl_apot(echo_ctx *c, const double *apot);
+void launch_prims_out(echo_ctx *c, double *out8);
+// mode 0: state sums, div B, non-finite count into dres[0..10]; mode 1: sum |a - b| into dres[0]
+void launch_diag_mode(echo_ctx *c, int mode, const double *a, const double *b);
+void launch_copy_state(echo_ctx *c, double *dst_u, double *dst_b, const double *src_u,
+                       const double *src_b);
+void launch_w_from_cold(echo_ctx *c);
+double probe_fma_peak(echo_ctx *c, int fp64);
+
+}  // namespace echo

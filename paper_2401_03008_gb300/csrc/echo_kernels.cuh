@@ -1,0 +1,403 @@
+// Kernels of one Runge-Kutta substep, templated on the reconstruction precision R
+// (double: FP64 path; float: mixed path).  Included by one translation unit per R.
+//
+// Work split (one thread per output value, x fastest so every stencil load of a
+// warp is a contiguous 32-element row):
+//   k_int_c2p   Sec. 3 step 1: INT of the staggered field + Newton inversion.
+//   k_flux<D>   Sec. 3 step 2: MP5 of the 8 primitives at the face above each
+//               cell along D, fluxes, fast speeds, HLL; UCT face data; max speed.
+//   k_der<D>    Sec. 3 step 3: rhs -= DER_D(flux).
+//   k_uct<C>    Sec. 3 step 4: four-state upwind edge field along C.
+//   k_rk        Sec. 3 step 4 (curl with DER) + step 5 (SSP-RK3 stage).
+#pragma once
+
+#include "echo_internal.h"
+
+namespace echo {
+
+constexpr int BS = 256;
+
+template <typename R>
+__device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// step 1: INT + C2P
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(BS)
+k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
+          double *__restrict__ W, const float *__restrict__ guess, R *__restrict__ prim,
+          C2PParams par, DevScalars *sc, int stage, long step, int update_w, int count)
+{
+    // the flag is set by other blocks of this launch: read it once per warp so that
+    // the warp-wide reductions below always see all 32 lanes
+    if (count && __reduce_or_sync(0xffffffffu, (unsigned)sc->halt)) return;
+    const long n = g.n;
+    long c = blockIdx.x * (long)BS + threadIdx.x;
+    unsigned it = 0;
+    bool active = c < n, bad = false, fb = false;
+    if (active) {
+        int i, j, k;
+        coords(g, c, i, j, k);
+        double B[3];
+        B[0] = int_c(Bf[shifted<0>(g, i, j, k, -2)], Bf[shifted<0>(g, i, j, k, -1)],
+                     Bf[c], Bf[shifted<0>(g, i, j, k, 1)], g.ho);
+        const double *By = Bf + n, *Bz = Bf + 2 * n;
+        B[1] = int_c(By[shifted<1>(g, i, j, k, -2)], By[shifted<1>(g, i, j, k, -1)],
+                     By[c], By[shifted<1>(g, i, j, k, 1)], g.ho);
+        B[2] = int_c(Bz[shifted<2>(g, i, j, k, -2)], Bz[shifted<2>(g, i, j, k, -1)],
+                     Bz[c], Bz[shifted<2>(g, i, j, k, 1)], g.ho);
+        double u[5];
+#pragma unroll
+        for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
+        double W0;
+        if (par.guess == 1) {
+            W0 = u[4];
+        } else if (par.guess == 2 && guess) {
+            W0 = (double)guess[c];
+            C2PInv q;
+            q.D = u[0];
+            q.S2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+            q.B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+            q.SB = u[1] * B[0] + u[2] * B[1] + u[3] * B[2];
+            q.U = u[4];
+            if (!c2p_ok(q, W0)) {
+                W0 = W[c];
+                fb = true;
+            }
+        } else {
+            W0 = W[c];
+        }
+        double p[5], Wn;
+        int iters;
+        bad = !c2p_newton(u, B, g.gam, W0, par.tol, par.maxit, p, Wn, iters);
+        it = (unsigned)iters;
+#pragma unroll
+        for (int v = 0; v < 5; v++) prim[v * n + c] = (R)p[v];
+#pragma unroll
+        for (int v = 0; v < 3; v++) prim[(5 + v) * n + c] = (R)B[v];
+        if (update_w) W[c] = Wn;
+    }
+    if (!count) return;
+    unsigned s = __reduce_add_sync(0xffffffffu, it);
+    unsigned m = __reduce_max_sync(0xffffffffu, it);
+    unsigned na = __popc(__ballot_sync(0xffffffffu, active));
+    unsigned nb = __popc(__ballot_sync(0xffffffffu, bad));
+    unsigned nf = __popc(__ballot_sync(0xffffffffu, fb));
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sc->it_sum, (unsigned long long)s);
+        atomicAdd(&sc->c2p_calls, (unsigned long long)na);
+        atomicMax(&sc->it_max, m);
+        if (nf) atomicAdd(&sc->fallbacks, nf);
+        if (nb) {
+            atomicAdd(&sc->fails, nb);
+            if (atomicCAS(&sc->fail_stage, 0, stage) == 0) sc->fail_step = step;
+            atomicOr(&sc->halt, 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// steps 2: reconstruction + HLL at the faces along D
+// ---------------------------------------------------------------------------
+template <typename R, int D>
+__global__ void __launch_bounds__(BS)
+k_flux(Grid g, const R *__restrict__ prim, const double *__restrict__ Bf, R *__restrict__ flux,
+       R *__restrict__ fd, DevScalars *sc, int want_amax)
+{
+    if (sc->halt) return;
+    const long n = g.n;
+    long f = blockIdx.x * (long)BS + threadIdx.x;
+    double amax = 0.0;
+    if (f < n) {
+        int i, j, k;
+        coords(g, f, i, j, k);
+        long cs[6];
+#pragma unroll
+        for (int m = 0; m < 6; m++) cs[m] = shifted<D>(g, i, j, k, m - 2);
+        R L[8], Rt[8];
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+            if (v == 5 + D) continue;
+            R s[6];
+#pragma unroll
+            for (int m = 0; m < 6; m++) s[m] = ld(prim + v * n + cs[m]);
+            mp5_lr(s, L[v], Rt[v]);
+        }
+        const R bn = (R)Bf[D * n + f];
+        L[5 + D] = bn;
+        Rt[5 + D] = bn;
+        // positivity: reset a state to the first-order (cell) value
+        int nfb = 0;
+        {
+            R v2 = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
+            if (!(L[0] > R(0)) || !(L[4] > R(0)) || !(v2 < R(1))) {
+#pragma unroll
+                for (int v = 0; v < 8; v++)
+                    if (v != 5 + D) L[v] = prim[v * n + cs[2]];
+                nfb++;
+            }
+            v2 = Rt[1] * Rt[1] + Rt[2] * Rt[2] + Rt[3] * Rt[3];
+            if (!(Rt[0] > R(0)) || !(Rt[4] > R(0)) || !(v2 < R(1))) {
+#pragma unroll
+                for (int v = 0; v < 8; v++)
+                    if (v != 5 + D) Rt[v] = prim[v * n + cs[3]];
+                nfb++;
+            }
+        }
+        if (nfb) atomicAdd(&sc->rec_fallbacks, (unsigned)nfb);
+        const R gam = (R)g.gam;
+        const R gfac = (R)(g.gam / (g.gam - 1.0));
+        R UL[8], FL[8], UR[8], FR[8], lmL, lpL, lmR, lpR;
+        phys<R, D>(L, gam, gfac, UL, FL, lmL, lpL);
+        phys<R, D>(Rt, gam, gfac, UR, FR, lmR, lpR);
+        R ap = rmax(R(0), rmax(lpL, lpR));
+        R am = rmax(R(0), rmax(-lmL, -lmR));
+        R s = ap + am;
+        if (s > R(0)) {
+            R is = R(1) / s;
+#pragma unroll
+            for (int q = 0; q < 5; q++)
+                flux[q * n + f] = (ap * FL[q] + am * FR[q] - ap * am * (UR[q] - UL[q])) * is;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 5; q++) flux[q * n + f] = R(0.5) * (FL[q] + FR[q]);
+        }
+        constexpr int E1 = (D + 1) % 3;
+        fd[f] = L[1 + D];
+        fd[n + f] = L[1 + E1];
+        fd[2 * n + f] = Rt[1 + D];
+        fd[3 * n + f] = Rt[1 + E1];
+        fd[4 * n + f] = ap;
+        fd[5 * n + f] = am;
+        amax = (double)rmax(ap, am);
+    }
+    if (want_amax) {
+        __shared__ double red[BS / 32];
+        double m = warp_max(amax);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < BS / 32 ? red[threadIdx.x] : 0.0;
+            v = warp_max(v);
+            if (threadIdx.x == 0 && v > 0.0)
+                atomicMax(&sc->amax_bits, (unsigned long long)__double_as_longlong(v));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// step 3: rhs -= DER_D(flux)
+// ---------------------------------------------------------------------------
+template <typename R, int D>
+__global__ void __launch_bounds__(BS)
+k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevScalars *sc)
+{
+    if (sc->halt) return;
+    const long n = g.n;
+    long c = blockIdx.x * (long)BS + threadIdx.x;
+    if (c >= n) return;
+    int i, j, k;
+    coords(g, c, i, j, k);
+    long fs[6];
+#pragma unroll
+    for (int m = 0; m < 6; m++) fs[m] = shifted<D>(g, i, j, k, m - 3);
+    const R ih = (R)g.inv_h[D];
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+        R s[6];
+#pragma unroll
+        for (int m = 0; m < 6; m++) s[m] = ld(flux + q * n + fs[m]);
+        R d = der_c(s, ih, g.ho);
+        rhs[q * n + c] = first ? -d : rhs[q * n + c] - d;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// step 4a: UCT edge field along C
+// ---------------------------------------------------------------------------
+template <typename R, int C>
+__global__ void __launch_bounds__(BS)
+k_uct(Grid g, const double *__restrict__ Bf, const R *__restrict__ fda, const R *__restrict__ fdb,
+      R *__restrict__ E, DevScalars *sc)
+{
+    if (sc->halt) return;
+    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    const long n = g.n;
+    long e = blockIdx.x * (long)BS + threadIdx.x;
+    if (e >= n) return;
+    int i, j, k;
+    coords(g, e, i, j, k);
+    long sb[6], sa[6];
+#pragma unroll
+    for (int m = 0; m < 6; m++) {
+        sb[m] = shifted<B>(g, i, j, k, m - 2);
+        sa[m] = shifted<A>(g, i, j, k, m - 2);
+    }
+    R va[2][2], vb[2][2], Ba[2], Bb[2], s[6];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+#pragma unroll
+        for (int m = 0; m < 6; m++) s[m] = ld(fda + (2 * q) * n + sb[m]);
+        mp5_lr(s, va[q][0], va[q][1]);
+#pragma unroll
+        for (int m = 0; m < 6; m++) s[m] = ld(fda + (2 * q + 1) * n + sb[m]);
+        mp5_lr(s, vb[q][0], vb[q][1]);
+    }
+#pragma unroll
+    for (int m = 0; m < 6; m++) s[m] = (R)Bf[A * n + sb[m]];
+    mp5_lr(s, Ba[0], Ba[1]);
+#pragma unroll
+    for (int m = 0; m < 6; m++) s[m] = (R)Bf[B * n + sa[m]];
+    mp5_lr(s, Bb[0], Bb[1]);
+    R apa = rmax(ld(fda + 4 * n + e), ld(fda + 4 * n + sb[3]));
+    R ama = rmax(ld(fda + 5 * n + e), ld(fda + 5 * n + sb[3]));
+    R apb = rmax(ld(fdb + 4 * n + e), ld(fdb + 4 * n + sa[3]));
+    R amb = rmax(ld(fdb + 5 * n + e), ld(fdb + 5 * n + sa[3]));
+    E[C * n + e] = uct_point(va, vb, Ba, Bb, apa, ama, apb, amb);
+}
+
+// curl of the edge field on the a-faces of cell (i,j,k): D_b E_c - D_c E_b
+template <typename R>
+__device__ __forceinline__ R curl_a(const Grid &g, const R *__restrict__ E, int a, int i, int j,
+                                    int k)
+{
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    const long n = g.n;
+    R s[6], t[6];
+#pragma unroll
+    for (int m = 0; m < 6; m++) {
+        s[m] = ld(E + c * n + shifted_rt(g, i, j, k, b, m - 3));
+        t[m] = ld(E + b * n + shifted_rt(g, i, j, k, c, m - 3));
+    }
+    return der_c(s, (R)g.inv_h[b], g.ho) - der_c(t, (R)g.inv_h[c], g.ho);
+}
+
+// ---------------------------------------------------------------------------
+// step 4b + 5: curl of E and the SSP-RK3 stage on 5 cell + 3 face variables
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(BS)
+k_rk(Grid g, int stage, const R *__restrict__ E, const R *__restrict__ rhs,
+     double *__restrict__ U, double *__restrict__ U0, double *__restrict__ Bf,
+     double *__restrict__ Bf0, DevScalars *sc)
+{
+    if (sc->halt) return;
+    const long n = g.n;
+    long c = blockIdx.x * (long)BS + threadIdx.x;
+    const double dt = sc->dt;
+    if (c < n) {
+        int i, j, k;
+        coords(g, c, i, j, k);
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+            double r, u, *pu, *pu0;
+            if (v < 5) {
+                r = (double)rhs[v * n + c];
+                pu = U + v * n + c;
+                pu0 = U0 + v * n + c;
+            } else {
+                r = -(double)curl_a(g, E, v - 5, i, j, k);
+                pu = Bf + (v - 5) * n + c;
+                pu0 = Bf0 + (v - 5) * n + c;
+            }
+            u = *pu;
+            if (stage == 1) {
+                *pu0 = u;
+                *pu = u + dt * r;
+            } else if (stage == 2) {
+                *pu = 0.75 * (*pu0) + 0.25 * (u + dt * r);
+            } else {
+                *pu = (*pu0) / 3.0 + 2.0 / 3.0 * (u + dt * r);
+            }
+        }
+    }
+    if (stage == 3 && blockIdx.x == 0 && threadIdx.x == 0) sc->step += 1;
+}
+
+// out (double) = sign * curl(E) on faces, accumulate or overwrite
+template <typename R>
+__global__ void __launch_bounds__(BS)
+k_curl(Grid g, const R *__restrict__ E, double *__restrict__ out, double sign, int accumulate)
+{
+    const long n = g.n;
+    long c = blockIdx.x * (long)BS + threadIdx.x;
+    if (c >= n) return;
+    int i, j, k;
+    coords(g, c, i, j, k);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        double v = sign * (double)curl_a(g, E, a, i, j, k);
+        out[a * n + c] = accumulate ? out[a * n + c] + v : v;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(BS) k_to_double(long m, const R *__restrict__ in, double *__restrict__ out)
+{
+    long q = blockIdx.x * (long)BS + threadIdx.x;
+    if (q < m) out[q] = (double)in[q];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename R>
+void Path<R>::int_c2p(echo_ctx *c, int stage, long step, int update_w)
+{
+    C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, c->cfg.c2p_guess};
+    if (par.guess == ECHO_GUESS_MLP && !c->guess) par.guess = ECHO_GUESS_PREV;
+    launch(c, K_C2P, k_int_c2p<R>, nblocks(c->g.n, BS), BS, 0, c->g, (const double *)c->U,
+           (const double *)c->Bf, c->W, (const float *)c->guess, (R *)c->prim, par, c->sc,
+           stage, step, update_w, 1);
+}
+
+template <typename R>
+void Path<R>::sweeps(echo_ctx *c, int want_amax)
+{
+    const unsigned nb = nblocks(c->g.n, BS);
+    const R *prim = (const R *)c->prim;
+    R *flux = (R *)c->flux, *rhs = (R *)c->rhs;
+    launch(c, K_FLUX_X, k_flux<R, 0>, nb, BS, 0, c->g, prim, (const double *)c->Bf, flux,
+           (R *)c->fdat[0], c->sc, want_amax);
+    launch(c, K_DER_X, k_der<R, 0>, nb, BS, 0, c->g, (const R *)flux, rhs, 1, c->sc);
+    launch(c, K_FLUX_Y, k_flux<R, 1>, nb, BS, 0, c->g, prim, (const double *)c->Bf, flux,
+           (R *)c->fdat[1], c->sc, want_amax);
+    launch(c, K_DER_Y, k_der<R, 1>, nb, BS, 0, c->g, (const R *)flux, rhs, 0, c->sc);
+    launch(c, K_FLUX_Z, k_flux<R, 2>, nb, BS, 0, c->g, prim, (const double *)c->Bf, flux,
+           (R *)c->fdat[2], c->sc, want_amax);
+    launch(c, K_DER_Z, k_der<R, 2>, nb, BS, 0, c->g, (const R *)flux, rhs, 0, c->sc);
+}
+
+template <typename R>
+void Path<R>::uct(echo_ctx *c)
+{
+    const unsigned nb = nblocks(c->g.n, BS);
+    const R *f0 = (const R *)c->fdat[0], *f1 = (const R *)c->fdat[1], *f2 = (const R *)c->fdat[2];
+    // E_z from x-faces (a) and y-faces (b); E_x from y and z; E_y from z and x
+    launch(c, K_UCT_Z, k_uct<R, 2>, nb, BS, 0, c->g, (const double *)c->Bf, f0, f1, (R *)c->E, c->sc);
+    launch(c, K_UCT_X, k_uct<R, 0>, nb, BS, 0, c->g, (const double *)c->Bf, f1, f2, (R *)c->E, c->sc);
+    launch(c, K_UCT_Y, k_uct<R, 1>, nb, BS, 0, c->g, (const double *)c->Bf, f2, f0, (R *)c->E, c->sc);
+}
+
+template <typename R>
+void Path<R>::rk(echo_ctx *c, int stage)
+{
+    launch(c, K_RK, k_rk<R>, nblocks(c->g.n, BS), BS, 0, c->g, stage, (const R *)c->E,
+           (const R *)c->rhs, c->U, c->U0, c->Bf, c->Bf0, c->sc);
+}
+
+template <typename R>
+void Path<R>::curl_out(echo_ctx *c, double *out)
+{
+    launch(c, K_CURL, k_curl<R>, nblocks(c->g.n, BS), BS, 0, c->g, (const R *)c->E, out, -1.0, 0);
+}
+
+template <typename R>
+void Path<R>::rhs_out(echo_ctx *c, double *out)
+{
+    long m = 5 * c->g.n;
+    launch(c, K_MISC, k_to_double<R>, nblocks(m, BS), BS, 0, m, (const R *)c->rhs, out);
+}
+
+}  // namespace echo

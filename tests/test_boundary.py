@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every entry point include/echo.h
+declares; argument checks that need no GPU behave as documented."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2401_03008_gb300 import echo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "echo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(echo_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared()
+    assert len(names) >= 17
+    L = echo.lib()
+    for name in names:
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", echo.lib_path()], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (echo_[a-z0-9_]+)", out))
+    assert set(names) <= exported, set(names) - exported
+    assert set(echo.EXPORTS) == set(names)
+
+
+def test_config_default():
+    cfg = echo.Config()
+    assert echo.lib().echo_config_default(C.byref(cfg)) == echo.ECHO_OK
+    assert (cfg.nx, cfg.uct, cfg.ho, cfg.precision) == (32, 1, 1, echo.FP64)
+    assert cfg.gamma_ad == pytest.approx(4 / 3) and cfg.cfl == 0.4 and cfg.c2p_tol == 1e-12
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("lz", -1.0), ("gamma_ad", 1.0),
+                                         ("cfl", 0.0), ("uct", 0), ("ho", 2), ("precision", 7),
+                                         ("c2p_guess", 5), ("c2p_maxit", 0)])
+def test_create_rejects_bad_config(field, value):
+    L = echo.lib()
+    cfg = echo.Config()
+    L.echo_config_default(C.byref(cfg))
+    setattr(cfg, field, value)
+    h = C.c_void_p()
+    assert L.echo_create(C.byref(cfg), C.byref(h)) == echo.ECHO_ERR_ARG
+    assert not h.value
+    assert L.echo_last_error(None)
+
+
+def test_null_arguments_rejected():
+    L = echo.lib()
+    assert L.echo_create(None, None) == echo.ECHO_ERR_ARG
+    assert L.echo_step(None, 1, 1.0, None, None) == echo.ECHO_ERR_ARG
+    assert L.echo_set_state(None, None, None, None, 0) == echo.ECHO_ERR_ARG
+    assert L.echo_destroy(None) == echo.ECHO_OK
+    assert L.echo_launches(None) == 0
+
+
+def test_create_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = echo.lib()
+    cfg = echo.Config()
+    L.echo_config_default(C.byref(cfg))
+    h = C.c_void_p()
+    assert L.echo_create(C.byref(cfg), C.byref(h)) == echo.ECHO_ERR_CUDA
+    with pytest.raises(echo.EchoError):
+        echo.Solver(8, 8, 8)
