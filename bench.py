@@ -236,7 +236,33 @@ def main():
     value = world * n ** 3 * args.steps / (ms * 1e-3)
     diag = s.diagnostics()
 
-    # per-kernel device time over a profiled pass (events on the launching stream)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic (analytic Alfven wave)", "config": workload_config(args),
+           "gpu_launches": launches, "clocks": clocks,
+           "diag": {"t": diag["t"], "divb_max": diag["divb_max"],
+                    "newton_it_mean": diag["newton_it_mean"],
+                    "c2p_failures": diag["c2p_failures"]}}
+    if args.prof_steps > 0:
+        out.update(roofline_and_profile(args, s, n))
+    if not args.no_e2e:
+        out["e2e"] = end_to_end(args, s, n, world)
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out))
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def roofline_and_profile(args, s, n):
+    """Per-kernel device time over a profiled pass (CUDA events recorded by the
+    library on its launching stream) and the roofline of the dominant kernel."""
+    import json as _json
     s.profile(True)
     s.profile_read(reset=True)
     s.step(args.prof_steps)
@@ -248,7 +274,6 @@ def main():
     per_launch_s = kms / cnt * 1e-3
 
     # roofline of the dominant kernel
-    import json as _json
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
@@ -282,43 +307,31 @@ def main():
         if tt:
             roof["traffic"] = tt * (units / 256 ** 3)
 
-    # end to end through the C ABI with host buffers: every step uploads the state
-    # from pinned host memory, advances one step and reads the state back
-    e2e = None
-    if not args.no_e2e:
-        pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
-        cons, bf, w = pin((5, n, n, n)), pin((3, n, n, n)), pin((n, n, n))
-        _, _, _, t0s, st0 = s.get_state(cons, bf, w)
-        ke = max(2, min(args.steps, 5))
-        torch.cuda.synchronize()
-        q0 = time.perf_counter()
-        for _ in range(ke):
-            s.set_conserved(cons, bf, w, t0s, st0)
-            s.step(1)
-            _, _, _, t0s, st0 = s.get_state(cons, bf, w)
-        el = time.perf_counter() - q0
-        by = (cons.nbytes + bf.nbytes + w.nbytes)
-        e2e = {"value": world * n ** 3 * ke / el, "unit": UNIT, "h2d_bytes_per_step": by,
-               "d2h_bytes_per_step": by, "steps": ke}
+    fp64_peak = s.probe_fma_peak("fp64")
+    fp32_peak = s.probe_fma_peak("fp32")
+    return {"roofline": roof, "kernel_ms_per_step":
+            {k: v[1] / args.prof_steps for k, v in sorted(prof.items())},
+            "measured_vector_peaks_tflops": {"fp64": fp64_peak / 1e12, "fp32": fp32_peak / 1e12}}
 
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-           "data": "synthetic (analytic Alfven wave)", "config": workload_config(args),
-           "roofline": roof, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
-           "kernel_ms_per_step": {k: v[1] / args.prof_steps for k, v in sorted(prof.items())},
-           "diag": {"t": diag["t"], "divb_max": diag["divb_max"],
-                    "newton_it_mean": diag["newton_it_mean"],
-                    "c2p_failures": diag["c2p_failures"]}}
-    if rank == 0 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(args)
-    if rank == 0:
-        print(json.dumps(out))
-    s.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+
+def end_to_end(args, s, n, world):
+    """The same metric through the C ABI with host buffers: every step uploads the
+    state from pinned host memory, advances one step and reads the state back."""
+    import torch
+    pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    cons, bf, w = pin((5, n, n, n)), pin((3, n, n, n)), pin((n, n, n))
+    _, _, _, t0s, st0 = s.get_state(cons, bf, w)
+    ke = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    q0 = time.perf_counter()
+    for _ in range(ke):
+        s.set_conserved(cons, bf, w, t0s, st0)
+        s.step(1)
+        _, _, _, t0s, st0 = s.get_state(cons, bf, w)
+    el = time.perf_counter() - q0
+    by = cons.nbytes + bf.nbytes + w.nbytes
+    return {"value": world * n ** 3 * ke / el, "unit": UNIT, "h2d_bytes_per_step": by,
+            "d2h_bytes_per_step": by, "steps": ke}
 
 
 if __name__ == "__main__":

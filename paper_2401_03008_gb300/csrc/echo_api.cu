@@ -163,7 +163,7 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     if (!(cfg->c2p_tol > 0.0) || cfg->c2p_maxit < 1)
         return fail(nullptr, ECHO_ERR_ARG, "c2p_tol must be > 0 and c2p_maxit >= 1");
     long n = (long)cfg->nx * cfg->ny * cfg->nz;
-    if (n > (1L << 40)) return fail(nullptr, ECHO_ERR_ARG, "grid too large");
+    if (n >= (1L << 31)) return fail(nullptr, ECHO_ERR_ARG, "grid too large (>= 2^31 cells)");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
         cudaGetLastError();

@@ -85,10 +85,12 @@ __device__ __forceinline__ long shifted_rt(const Grid &g, int i, int j, int k, i
 
 __device__ __forceinline__ void coords(const Grid &g, long c, int &i, int &j, int &k)
 {
-    long q = c / g.nx;
-    i = (int)(c - q * g.nx);
-    k = (int)(q / g.ny);
-    j = (int)(q - (long)k * g.ny);
+    // the library limits grids to < 2^31 cells, so 32-bit division suffices
+    unsigned cu = (unsigned)c, q = cu / (unsigned)g.nx;
+    i = (int)(cu - q * (unsigned)g.nx);
+    unsigned kk = q / (unsigned)g.ny;
+    k = (int)kk;
+    j = (int)(q - kk * (unsigned)g.ny);
 }
 
 // ---------------------------------------------------------------------------
@@ -154,19 +156,16 @@ __device__ __forceinline__ R int_c(R a, R b, R c, R d, int ho)
     return R(0.5) * (b + c);
 }
 
-// DER: derivative at a centre from staggered values s[0..5] at i-5/2..i+5/2;
-// high order corrects each staggered value by -d2/24 + 3 d4/640 first.
+// DER: derivative at a centre from staggered values s[0..5] at i-5/2..i+5/2.
+// High order corrects each staggered value by -d2/24 + 3 d4/640 before the
+// difference; expanded, the two corrected values combine into the single stencil
+// (75/64 (s3-s2) - 25/384 (s4-s1) + 3/640 (s5-s0)) / h, used here (no divisions).
 template <typename R>
 __device__ __forceinline__ R der_c(const R *s, R inv_h, int ho)
 {
     if (!ho) return (s[3] - s[2]) * inv_h;
-    R d2p = s[2] - R(2) * s[3] + s[4];
-    R d4p = s[1] - R(4) * s[2] + R(6) * s[3] - R(4) * s[4] + s[5];
-    R d2m = s[1] - R(2) * s[2] + s[3];
-    R d4m = s[0] - R(4) * s[1] + R(6) * s[2] - R(4) * s[3] + s[4];
-    R fp = s[3] - d2p / R(24) + R(3) * d4p / R(640);
-    R fm = s[2] - d2m / R(24) + R(3) * d4m / R(640);
-    return (fp - fm) * inv_h;
+    const R c0 = R(75.0 / 64.0), c1 = R(25.0 / 384.0), c2 = R(3.0 / 640.0);
+    return (c0 * (s[3] - s[2]) - c1 * (s[4] - s[1]) + c2 * (s[5] - s[0])) * inv_h;
 }
 
 // ---------------------------------------------------------------------------
@@ -183,8 +182,8 @@ __device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &l
     const R bx = s[5], by = s[6], bz = s[7];
     R v2 = vx * vx + vy * vy + vz * vz;
     R omv2 = R(1) - v2;
-    R lor2 = R(1) / omv2;
-    R lor = sqrt(lor2);
+    R lor = rsqrt(omv2);
+    R lor2 = lor * lor;
     R rhoh = rho + gfac * pg;
     R w = rhoh * lor2;
     // E = -v x B
@@ -217,11 +216,14 @@ __device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &l
     F[5] = vd * bx - vx * Bd;
     F[6] = vd * by - vy * Bd;
     F[7] = vd * bz - vz * Bd;
-    // approximate fast magnetosonic speeds
-    R cs2 = gam * pg / rhoh;
+    // approximate fast magnetosonic speeds; 1/rhoh and 1/(rhoh + b^2) from one
+    // reciprocal of their product
     R vb = vx * bx + vy * by + vz * bz;
     R bb2 = b2 * omv2 + vb * vb;
-    R ca2 = bb2 / (rhoh + bb2);
+    R den = rhoh + bb2;
+    R rr = R(1) / (rhoh * den);
+    R cs2 = gam * pg * den * rr;
+    R ca2 = bb2 * rhoh * rr;
     R w2 = cs2 + ca2 - cs2 * ca2;
     R disc = w2 * omv2 * ((R(1) - v2 * w2) - vd * vd * (R(1) - w2));
     disc = disc < R(0) ? R(0) : disc;
@@ -242,6 +244,7 @@ __device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const
 {
     R sa = apa + ama, sb = apb + amb;
     R e4 = R(0);
+    R isa = R(0), isb = R(0);
     if (sa > R(0) && sb > R(0)) {
         R wa[2] = {apa, ama}, wb[2] = {apb, amb};
 #pragma unroll
@@ -249,7 +252,10 @@ __device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const
 #pragma unroll
             for (int t = 0; t < 2; t++)
                 e4 += wa[s] * wb[t] * (vb[s][t] * Ba[t] - va[s][t] * Bb[s]);
-        e4 = e4 / (sa * sb);
+        R r = R(1) / (sa * sb);
+        e4 = e4 * r;
+        isa = sb * r;
+        isb = sa * r;
     } else {
 #pragma unroll
         for (int s = 0; s < 2; s++)
@@ -257,8 +263,10 @@ __device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const
             for (int t = 0; t < 2; t++)
                 e4 += R(0.25) * (vb[s][t] * Ba[t] - va[s][t] * Bb[s]);
     }
-    R da = sa > R(0) ? apa * ama * (Bb[1] - Bb[0]) / sa : R(0);
-    R db = sb > R(0) ? apb * amb * (Ba[1] - Ba[0]) / sb : R(0);
+    if (sa > R(0) && !(sb > R(0))) isa = R(1) / sa;
+    if (sb > R(0) && !(sa > R(0))) isb = R(1) / sb;
+    R da = apa * ama * (Bb[1] - Bb[0]) * isa;
+    R db = apb * amb * (Ba[1] - Ba[0]) * isb;
     return e4 + da - db;
 }
 
@@ -269,19 +277,27 @@ struct C2PInv {
     double D, S2, B2, SB, U, gm1g;
 };
 
-__device__ __forceinline__ double c2p_v2(const C2PInv &q, double W)
+// v^2(W) and r = 1/(W (W + B^2)); valid when W > 0, finite and v^2 < 1
+__device__ __forceinline__ bool c2p_eval(const C2PInv &q, double W, double &v2, double &r)
 {
+    if (!(W > 0.0) || !isfinite(W)) return false;
     double wb = W + q.B2;
-    return (q.S2 * W * W + q.SB * q.SB * (q.B2 + 2.0 * W)) / (W * W * wb * wb);
+    r = 1.0 / (W * wb);
+    v2 = (q.S2 * W * W + q.SB * q.SB * (q.B2 + 2.0 * W)) * (r * r);
+    return isfinite(v2) && v2 < 1.0;
 }
 
 __device__ __forceinline__ bool c2p_ok(const C2PInv &q, double W)
 {
-    if (!(W > 0.0) || !isfinite(W)) return false;
-    double v2 = c2p_v2(q, W);
-    return isfinite(v2) && v2 < 1.0;
+    double v2, r;
+    return c2p_eval(q, W, v2, r);
 }
 
+// Newton on f(W) = W - p(W) + (1 + v^2) B^2/2 - (S.B)^2/(2 W^2) - U with the
+// analytic derivative; a trial point outside the domain halves the step; stop
+// when |dW| <= tol W, after one more polishing step.  The domain check of a trial
+// point computes v^2 and 1/(W (W+B^2)) there, and the next iteration reuses both,
+// so an iteration costs two divisions and one reciprocal square root.
 // Returns true on success.  prim = (rho, vx, vy, vz, p); B the cell-centred field.
 __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, double gam,
                                            double W0, double tol, int maxit, double *prim,
@@ -294,34 +310,45 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     q.SB = u[1] * B[0] + u[2] * B[1] + u[3] * B[2];
     q.U = u[4];
     q.gm1g = (gam - 1.0) / gam;
-    double W = W0;
-    for (int k = 0; k < 64 && !c2p_ok(q, W); k++)
+    const double SB2 = q.SB * q.SB;
+    double W = W0, v2 = 0.0, r = 0.0;
+    bool ok = c2p_eval(q, W, v2, r);
+    for (int k = 0; k < 64 && !ok; k++) {
         W = (W > 0.0 && isfinite(W)) ? 2.0 * W : fabs(q.U) + 1.0;
+        ok = c2p_eval(q, W, v2, r);
+    }
     int it = 0;
     bool conv = false, polish = false;
-    const double SB2 = q.SB * q.SB;
-    while (it < maxit) {
-        double iW = 1.0 / W;
+    while (ok && it < maxit) {
         double wb = W + q.B2;
-        double iwb = 1.0 / wb;
-        double v2 = (q.S2 * W * W + SB2 * (q.B2 + 2.0 * W)) * (iW * iW) * (iwb * iwb);
-        double sq1 = sqrt(1.0 - v2);
-        double p = q.gm1g * (W * (1.0 - v2) - q.D * sq1);
-        double dv2 = -2.0 * SB2 * (iW * iW * iW) * iwb - 2.0 * v2 * iwb;
-        double dp = q.gm1g * ((1.0 - v2) - W * dv2 + q.D * dv2 / (2.0 * sq1));
-        double f = W - p + 0.5 * (1.0 + v2) * q.B2 - 0.5 * SB2 * (iW * iW) - q.U;
-        double df = 1.0 - dp + 0.5 * q.B2 * dv2 + SB2 * (iW * iW * iW);
+        double iW = wb * r, iwb = W * r;
+        double omv2 = 1.0 - v2;
+        double isq = rsqrt(omv2);
+        double sq1 = omv2 * isq;
+        double iW2 = iW * iW;
+        double p = q.gm1g * (W * omv2 - q.D * sq1);
+        double dv2 = -2.0 * SB2 * (iW2 * iW) * iwb - 2.0 * v2 * iwb;
+        double dp = q.gm1g * (omv2 - W * dv2 + 0.5 * q.D * dv2 * isq);
+        double f = W - p + 0.5 * (1.0 + v2) * q.B2 - 0.5 * SB2 * iW2 - q.U;
+        double df = 1.0 - dp + 0.5 * q.B2 * dv2 + SB2 * (iW2 * iW);
         double dW = -f / df;
         if (!isfinite(dW)) break;
-        double lam = 1.0, Wn = W + dW;
-        for (int k = 0; k < 60 && !c2p_ok(q, Wn); k++) {
+        double lam = 1.0, Wn = W + dW, v2n, rn;
+        bool okn = c2p_eval(q, Wn, v2n, rn);
+        for (int k = 0; k < 60 && !okn; k++) {
             lam *= 0.5;
             Wn = W + lam * dW;
+            okn = c2p_eval(q, Wn, v2n, rn);
         }
         it++;
-        if (!c2p_ok(q, Wn)) break;
+        if (!okn) {
+            ok = false;
+            break;
+        }
         double step = fabs(Wn - W);
         W = Wn;
+        v2 = v2n;
+        r = rn;
         if (polish) {
             conv = true;
             break;
@@ -330,16 +357,17 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     }
     iters = it;
     Wout = W;
-    double v2 = c2p_v2(q, W);
-    double sq1 = sqrt(1.0 - v2);
-    double p = q.gm1g * (W * (1.0 - v2) - q.D * sq1);
+    if (!ok) v2 = fmin(fmax(v2, 0.0), 1.0);
+    double omv2 = 1.0 - v2;
+    double sq1 = sqrt(omv2);
+    double p = q.gm1g * (W * omv2 - q.D * sq1);
     double rho = q.D * sq1;
     double wb = W + q.B2;
-    double iW = 1.0 / W;
-    for (int i = 0; i < 3; i++) prim[1 + i] = (u[1 + i] + q.SB * B[i] * iW) / wb;
+    double iW = wb * r, iwb = W * r;
+    for (int i = 0; i < 3; i++) prim[1 + i] = (u[1 + i] + q.SB * B[i] * iW) * iwb;
     prim[0] = rho;
     prim[4] = p;
-    return conv && isfinite(p) && isfinite(rho) && p > 0.0 && rho > 0.0 && v2 < 1.0;
+    return ok && conv && isfinite(p) && isfinite(rho) && p > 0.0 && rho > 0.0 && v2 < 1.0;
 }
 
 // ---------------------------------------------------------------------------

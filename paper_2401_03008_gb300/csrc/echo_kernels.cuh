@@ -308,7 +308,7 @@ k_rk(Grid g, int stage, const R *__restrict__ E, const R *__restrict__ rhs,
             } else if (stage == 2) {
                 *pu = 0.75 * (*pu0) + 0.25 * (u + dt * r);
             } else {
-                *pu = (*pu0) / 3.0 + 2.0 / 3.0 * (u + dt * r);
+                *pu = (*pu0) * (1.0 / 3.0) + 2.0 / 3.0 * (u + dt * r);
             }
         }
     }
