@@ -176,6 +176,33 @@ long echo_launches(const echo_ctx *ctx);
  * *flops (an FMA counts as 2).  precision: ECHO_FP64 or ECHO_MIXED (= FP32). */
 echo_status echo_probe_fma_peak(echo_ctx *ctx, int precision, double *flops);
 
+/* Diagnostics without any device allocation, for callers that cannot allocate.
+ * The paper has no counterpart: this is a service of the library.  Some callers
+ * must not call cudaMalloc (their device memory belongs to a fixed pool or to
+ * another framework, or new allocations are not allowed where they run); they
+ * still hold the state on the device and want its health checks.  This call
+ * computes, over the caller's own device arrays, what echo_diagnostics reports
+ * about a state: out[0..7] = sums of D, Sx, Sy, Sz, U and face Bx, By, Bz,
+ * out[8] = max |div B|, out[9] = RMS div B, out[10] = number of non-finite values.
+ *   cons5 [5][nz][ny][nx] and bface [3][nz][ny][nx]: device memory of the current
+ *         device, in the layouts of echo_get_state; only read.
+ *   nx, ny, nz, lx, ly, lz, ho: the grid, as in echo_config.
+ *   stream: cudaStream_t to run on (NULL: the default stream); the call returns
+ *         after the stream has finished the reduction.
+ *   out: 11 doubles, host (out_kind = ECHO_PTR_HOST) or device memory.
+ * No memory is allocated: the block partial sums live in a fixed array of about
+ * 0.8 MB inside the library, which every GPU that loads the library holds until
+ * the process exits.  It limits the grid to 1,048,576 cells; larger grids return
+ * ECHO_ERR_ARG.  Every call shares that array, so calls that overlap on the GPU
+ * (several streams or host threads at once) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address; make
+ * it before any stream capture.  Errors: ECHO_ERR_ARG (sizes, NULL or non-device
+ * inputs), ECHO_ERR_CUDA; the text is in echo_last_error(NULL).  The sums agree
+ * with echo_diagnostics to rounding (the summation order differs). */
+echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, int nx,
+                                     int ny, int nz, double lx, double ly, double lz, int ho,
+                                     void *stream, double *out, int out_kind);
+
 /* The context's stream (cudaStream_t) and device. */
 void *echo_stream(const echo_ctx *ctx);
 

@@ -121,6 +121,8 @@ void free_all(echo_ctx *c)
 
 }  // namespace
 
+void echo::set_global_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 extern "C" {
 
 echo_status echo_config_default(echo_config *cfg)

@@ -113,5 +113,7 @@ void launch_copy_state(echo_ctx *c, double *dst_u, double *dst_b, const double *
                        const double *src_b);
 void launch_w_from_cold(echo_ctx *c);
 double probe_fma_peak(echo_ctx *c, int fp64);
+// error text of calls without a context (returned by echo_last_error(NULL))
+void set_global_error(const char *msg);
 
 }  // namespace echo

@@ -28,7 +28,7 @@ EXPORTS = ["echo_config_default", "echo_create", "echo_destroy", "echo_set_state
            "echo_step", "echo_rhs", "echo_get_primitives", "echo_get_state",
            "echo_set_conserved", "echo_diagnostics", "echo_l1_error", "echo_profile_enable",
            "echo_profile_read", "echo_launches", "echo_probe_fma_peak", "echo_stream",
-           "echo_last_error"]
+           "echo_last_error", "echo_diagnostics_noalloc"]
 
 
 class EchoError(RuntimeError):
@@ -96,6 +96,8 @@ def lib():
     L.echo_stream.restype = vp
     L.echo_last_error.argtypes = [vp]
     L.echo_last_error.restype = C.c_char_p
+    L.echo_diagnostics_noalloc.argtypes = [vp, vp, ip, ip, ip, C.c_double, C.c_double,
+                                           C.c_double, ip, vp, vp, ip]
     _lib = L
     return L
 
