@@ -97,22 +97,46 @@ __device__ __forceinline__ void coords(const Grid &g, long c, int &i, int &j, in
 // 1-D operators (REC, INT, DER of Sec. 3)
 // ---------------------------------------------------------------------------
 
-template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
-template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+// Comparisons.  On GB300 the FP64 pipe issues two thread operations per clock per
+// SM and a double compare (DSETP) costs as much there as an FMA.  A double maps to
+// an ordered 64-bit integer key (the sign-magnitude bits with the magnitude
+// flipped for negative values), so compares, min and max of doubles run on the
+// integer pipe instead; exact for every non-NaN value (+0 and -0 order as -0 < +0,
+// which no result here depends on).  float keeps the native compares.
+__device__ __forceinline__ long long okey(double x)
+{
+    long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool gtz(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool ltz(double x) { return okey(x) < -1; }
+__device__ __forceinline__ bool lt(double a, double b) { return okey(a) < okey(b); }
+__device__ __forceinline__ bool le(double a, double b) { return okey(a) <= okey(b); }
+__device__ __forceinline__ bool finite64(double x)
+{
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool gtz(float x) { return x > 0.f; }
+__device__ __forceinline__ bool ltz(float x) { return x < 0.f; }
+__device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool le(float a, float b) { return a <= b; }
+
+template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return lt(a, b) ? a : b; }
+template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return lt(b, a) ? a : b; }
 
 template <typename R>
 __device__ __forceinline__ R minmod2(R a, R b)
 {
-    if (a > R(0) && b > R(0)) return rmin(a, b);
-    if (a < R(0) && b < R(0)) return rmax(a, b);
+    if (gtz(a) && gtz(b)) return rmin(a, b);
+    if (ltz(a) && ltz(b)) return rmax(a, b);
     return R(0);
 }
 
 template <typename R>
 __device__ __forceinline__ R minmod4(R a, R b, R c, R d)
 {
-    if (a > R(0) && b > R(0) && c > R(0) && d > R(0)) return rmin(rmin(a, b), rmin(c, d));
-    if (a < R(0) && b < R(0) && c < R(0) && d < R(0)) return rmax(rmax(a, b), rmax(c, d));
+    if (gtz(a) && gtz(b) && gtz(c) && gtz(d)) return rmin(rmin(a, b), rmin(c, d));
+    if (ltz(a) && ltz(b) && ltz(c) && ltz(d)) return rmax(rmax(a, b), rmax(c, d));
     return R(0);
 }
 
@@ -125,7 +149,7 @@ __device__ __forceinline__ R mp5(R um2, R um1, R u0, R up1, R up2)
     const R alpha = R(4);
     R uor = (R(3) * um2 - R(20) * um1 + R(90) * u0 + R(60) * up1 - R(5) * up2) * R(0.0078125);
     R ump = u0 + minmod2(up1 - u0, alpha * (u0 - um1));
-    if ((uor - u0) * (uor - ump) <= R(1e-10)) return uor;
+    if (le((uor - u0) * (uor - ump), R(1e-10))) return uor;
     R djm1 = um2 - R(2) * um1 + u0;
     R dj = um1 - R(2) * u0 + up1;
     R djp1 = u0 - R(2) * up1 + up2;
@@ -226,7 +250,7 @@ __device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &l
     R ca2 = bb2 * rhoh * rr;
     R w2 = cs2 + ca2 - cs2 * ca2;
     R disc = w2 * omv2 * ((R(1) - v2 * w2) - vd * vd * (R(1) - w2));
-    disc = disc < R(0) ? R(0) : disc;
+    disc = ltz(disc) ? R(0) : disc;
     R sr = sqrt(disc);
     R inv = R(1) / (R(1) - v2 * w2);
     lp = (vd * (R(1) - w2) + sr) * inv;
@@ -245,7 +269,8 @@ __device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const
     R sa = apa + ama, sb = apb + amb;
     R e4 = R(0);
     R isa = R(0), isb = R(0);
-    if (sa > R(0) && sb > R(0)) {
+    const bool pa = gtz(sa), pb = gtz(sb);
+    if (pa && pb) {
         R wa[2] = {apa, ama}, wb[2] = {apb, amb};
 #pragma unroll
         for (int s = 0; s < 2; s++)
@@ -263,8 +288,8 @@ __device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const
             for (int t = 0; t < 2; t++)
                 e4 += R(0.25) * (vb[s][t] * Ba[t] - va[s][t] * Bb[s]);
     }
-    if (sa > R(0) && !(sb > R(0))) isa = R(1) / sa;
-    if (sb > R(0) && !(sa > R(0))) isb = R(1) / sb;
+    if (pa && !pb) isa = R(1) / sa;
+    if (pb && !pa) isb = R(1) / sb;
     R da = apa * ama * (Bb[1] - Bb[0]) * isa;
     R db = apb * amb * (Ba[1] - Ba[0]) * isb;
     return e4 + da - db;
@@ -280,11 +305,11 @@ struct C2PInv {
 // v^2(W) and r = 1/(W (W + B^2)); valid when W > 0, finite and v^2 < 1
 __device__ __forceinline__ bool c2p_eval(const C2PInv &q, double W, double &v2, double &r)
 {
-    if (!(W > 0.0) || !isfinite(W)) return false;
+    if (!gtz(W) || !finite64(W)) return false;
     double wb = W + q.B2;
     r = 1.0 / (W * wb);
     v2 = (q.S2 * W * W + q.SB * q.SB * (q.B2 + 2.0 * W)) * (r * r);
-    return isfinite(v2) && v2 < 1.0;
+    return finite64(v2) && lt(v2, 1.0);
 }
 
 __device__ __forceinline__ bool c2p_ok(const C2PInv &q, double W)
@@ -314,7 +339,7 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     double W = W0, v2 = 0.0, r = 0.0;
     bool ok = c2p_eval(q, W, v2, r);
     for (int k = 0; k < 64 && !ok; k++) {
-        W = (W > 0.0 && isfinite(W)) ? 2.0 * W : fabs(q.U) + 1.0;
+        W = (gtz(W) && finite64(W)) ? 2.0 * W : fabs(q.U) + 1.0;
         ok = c2p_eval(q, W, v2, r);
     }
     int it = 0;
@@ -332,7 +357,7 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
         double f = W - p + 0.5 * (1.0 + v2) * q.B2 - 0.5 * SB2 * iW2 - q.U;
         double df = 1.0 - dp + 0.5 * q.B2 * dv2 + SB2 * (iW2 * iW);
         double dW = -f / df;
-        if (!isfinite(dW)) break;
+        if (!finite64(dW)) break;
         double lam = 1.0, Wn = W + dW, v2n, rn;
         bool okn = c2p_eval(q, Wn, v2n, rn);
         for (int k = 0; k < 60 && !okn; k++) {
@@ -353,7 +378,7 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
             conv = true;
             break;
         }
-        if (step <= tol * W) polish = true;
+        if (le(step, tol * W)) polish = true;
     }
     iters = it;
     Wout = W;
@@ -367,7 +392,7 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     for (int i = 0; i < 3; i++) prim[1 + i] = (u[1 + i] + q.SB * B[i] * iW) * iwb;
     prim[0] = rho;
     prim[4] = p;
-    return ok && conv && isfinite(p) && isfinite(rho) && p > 0.0 && rho > 0.0 && v2 < 1.0;
+    return ok && conv && finite64(p) && finite64(rho) && gtz(p) && gtz(rho) && lt(v2, 1.0);
 }
 
 // ---------------------------------------------------------------------------

@@ -131,14 +131,14 @@ k_flux(Grid g, const R *__restrict__ prim, const double *__restrict__ Bf, R *__r
         int nfb = 0;
         {
             R v2 = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
-            if (!(L[0] > R(0)) || !(L[4] > R(0)) || !(v2 < R(1))) {
+            if (!gtz(L[0]) || !gtz(L[4]) || !lt(v2, R(1))) {
 #pragma unroll
                 for (int v = 0; v < 8; v++)
                     if (v != 5 + D) L[v] = prim[v * n + cs[2]];
                 nfb++;
             }
             v2 = Rt[1] * Rt[1] + Rt[2] * Rt[2] + Rt[3] * Rt[3];
-            if (!(Rt[0] > R(0)) || !(Rt[4] > R(0)) || !(v2 < R(1))) {
+            if (!gtz(Rt[0]) || !gtz(Rt[4]) || !lt(v2, R(1))) {
 #pragma unroll
                 for (int v = 0; v < 8; v++)
                     if (v != 5 + D) Rt[v] = prim[v * n + cs[3]];
@@ -154,7 +154,7 @@ k_flux(Grid g, const R *__restrict__ prim, const double *__restrict__ Bf, R *__r
         R ap = rmax(R(0), rmax(lpL, lpR));
         R am = rmax(R(0), rmax(-lmL, -lmR));
         R s = ap + am;
-        if (s > R(0)) {
+        if (gtz(s)) {
             R is = R(1) / s;
 #pragma unroll
             for (int q = 0; q < 5; q++)
