@@ -68,7 +68,7 @@ enum { ECHO_GUESS_PREV = 0, ECHO_GUESS_COLD = 1, ECHO_GUESS_MLP = 2 };
 typedef struct {
     int nx, ny, nz;     /* cells per direction, periodic; each >= 1 */
     double lx, ly, lz;  /* box lengths (> 0) */
-    double gamma_ad;    /* adiabatic index of the ideal-gas law (Sec. 2, Eq. 7) */
+    double gamma_ad;    /* adiabatic index of the ideal-gas law (Sec. 2, Eq. 6) */
     double cfl;         /* dt = cfl * min(h) / max fast speed (Sec. 3 step 5) */
     int uct;            /* must be 1: staggered field evolved by UCT (Sec. 3) */
     int ho;             /* 1: fourth-order INT and sixth-order DER; 0: two-point forms */

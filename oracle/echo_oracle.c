@@ -9,7 +9,8 @@
  *   1. INT of the staggered field to cell centres, then the Newton C2P inversion;
  *   2. REC (MP5) of primitives at every interface, physical fluxes, HLL flux,
  *      fast speeds and the face data needed by UCT;
- *   3. DER of the numerical fluxes (flat space: no source terms, Sec. 2 Eq. 1-6);
+ *   3. DER of the numerical fluxes (flat space, Sec. 2: every source term of
+ *      Eq. 4 holds a metric derivative, so none remains);
  *   4. UCT edge electric fields and their curl (DER again);
  *   5. the Runge-Kutta stage update and, once per step, the timestep.
  * Where the paper only names a method, the textbook form used here is stated at
@@ -39,7 +40,7 @@
 typedef struct {
     int nx, ny, nz;
     double lx, ly, lz;
-    double gam;          /* adiabatic index of the ideal-gas law (Sec. 2, Eq. 7) */
+    double gam;          /* adiabatic index of the ideal-gas law (Sec. 2, Eq. 6) */
     double cfl;
     int uct;             /* 1: staggered B evolved by UCT; 0: cell-centred B */
     int ho;              /* 1: high-order INT and DER; 0: two-point forms */
@@ -110,7 +111,7 @@ static void efield(const double *v, const double *B, double *E)
 }
 
 /* Conserved variables from primitives (Sec. 2 definitions after Eq. 5 and the
- * ideal-gas enthalpy Eq. 7): D = rho*G, S = rho*h*G^2 v + E x B,
+ * ideal-gas enthalpy Eq. 6): D = rho*G, S = rho*h*G^2 v + E x B,
  * U = rho*h*G^2 - p + (E^2+B^2)/2.  prim = (rho, vx, vy, vz, p). */
 void orc_prim2cons(const double *prim, const double *B, double gam, double *u)
 {
@@ -235,7 +236,7 @@ static double minmod4(double a, double b, double c, double d)
     return 0.0;
 }
 
-/* MP5 (Sec. 3, the five-point REC named after Eq. 10): the value at i+1/2 from
+/* MP5 (Sec. 3, the five-point REC of the list of substep steps): the value at i+1/2 from
  * s = (u_{i-2}, ..., u_{i+2}), following Suresh & Huynh (1997).  The unlimited
  * value is the fifth-order point-value Lagrange interpolant at i+1/2, weights
  * (3, -20, 90, 60, -5)/128, since ECHO reconstructs point values.  The
@@ -420,7 +421,7 @@ long orc_c2p_batch(long n, const double *u, const double *B, const double *W0,
 }
 
 /* ------------------------------------------------------------------------- */
-/* UCT edge field (Sec. 3 step 4; Eq. 9)                                      */
+/* UCT edge field (Sec. 3 step 4; Eq. 10)                                     */
 /* ------------------------------------------------------------------------- */
 /* Upwind constrained transport, four-state form (Londrillo & Del Zanna 2004,
  * Del Zanna et al. 2007) for the edge along c at (a+1/2, b+1/2), (a, b, c) cyclic:
