@@ -165,7 +165,7 @@ echo_status echo_l1_error(echo_ctx *ctx, const double *ref, int ptr_kind, double
  * returns, for kernel kind k (0 <= k < ECHO_NKERNELS), its launch count and summed
  * device time in ms, and its name in *name; the counters are then cleared when
  * reset != 0.  echo_launches returns the number of kernels launched so far. */
-#define ECHO_NKERNELS 16
+#define ECHO_NKERNELS 20
 echo_status echo_profile_enable(echo_ctx *ctx, int on);
 echo_status echo_profile_read(echo_ctx *ctx, int k, long *launches, double *ms,
                               const char **name, int reset);
@@ -175,6 +175,55 @@ long echo_launches(const echo_ctx *ctx);
  * independent-FMA-chain kernel on the context's device and returns FLOP/s in
  * *flops (an FMA counts as 2).  precision: ECHO_FP64 or ECHO_MIXED (= FP32). */
 echo_status echo_probe_fma_peak(echo_ctx *ctx, int precision, double *flops);
+
+/* ---- The learned Newton starting guess (the benchmark spec's extension; the paper
+ * has no learned component).  Network 5 -> 64 -> 64 -> 1 with tanh hidden layers
+ * on five rotation-invariant, dimensionless features of a cell's conserved state
+ * (D/U, S^2/U^2, B^2/U, (S.B)^2/(S^2 B^2), ln(U/D)); output y = W/U and guess
+ * W0 = U y.  Parameters: a flat float array of ECHO_MLP_NPARAM values in the order
+ * W1[64][5], b1[64], W2[64][64], b2[64], w3[64], b3.  The 64x64 products run as
+ * BF16 tensor-core MMAs with FP32 accumulation.  The Newton iteration always runs
+ * to tolerance: the guess changes iteration counts, not results. ---- */
+#define ECHO_MLP_NPARAM 4609
+
+typedef struct {
+    int epochs;          /* passes over the data */
+    int batch;           /* minibatch size, a multiple of 64 */
+    double lr, beta1, beta2, eps;  /* Adam */
+    double lr_decay;     /* learning rate multiplied by this after every epoch */
+    unsigned long seed;  /* offset of the per-epoch batch permutation */
+} echo_train_cfg;
+
+/* Load parameters (host, n = ECHO_MLP_NPARAM floats) into the context; used when
+ * c2p_guess = ECHO_GUESS_MLP.  Cells whose guess is unusable fall back to the
+ * previous W and are counted (echo_diag.c2p_fallbacks). */
+echo_status echo_mlp_load(echo_ctx *ctx, const float *weights, long n);
+
+/* Inference on its own: y[n] (device) for features feats[n][5] (device) with the
+ * parameters weights (host), on stream (NULL: default stream). */
+echo_status echo_mlp_forward(const float *weights, const float *feats, long n, float *y,
+                             void *stream);
+
+/* Mean squared loss of y against target[n] (device) and its gradient grad[4609]
+ * (host) for parameters weights (host) over the n samples feats[n][5] (device);
+ * n a multiple of 64.  Same kernels as training. */
+echo_status echo_mlp_grad(const float *weights, const float *feats, const float *target, long n,
+                          float *grad, float *loss, void *stream);
+
+/* Train with Adam on the GPU: feats[n][5], target[n] (device, e.g. from
+ * echo_mlp_harvest); weights (host) hold the initial parameters on entry and the
+ * trained ones on exit; loss_hist[epochs] (host, may be NULL) the mean loss of
+ * each epoch. */
+echo_status echo_mlp_train(const float *feats, const float *target, long n,
+                           const echo_train_cfg *cfg, float *weights, float *loss_hist,
+                           void *stream);
+
+/* Advance nsteps SSP-RK3 steps (as echo_step) and, after every inversion, append the
+ * features and the converged W/U of every stride-th cell (offset rotating between
+ * calls) to feats[capacity][5] and target[capacity] (device).  *count receives the
+ * number of states written (at most capacity). */
+echo_status echo_mlp_harvest(echo_ctx *ctx, int nsteps, long stride, float *feats, float *target,
+                             long capacity, long *count);
 
 /* Diagnostics without any device allocation, for callers that cannot allocate.
  * The paper has no counterpart: this is a service of the library.  Some callers

@@ -1,0 +1,98 @@
+"""FP64 oracle of the learned Newton starting guess (test infrastructure only).
+
+The paper has no learned component; this follows the project's definition of it.
+Network: 5 -> 64 -> 64 -> 1, tanh on both hidden layers, linear output.
+Parameters (one flat float vector, 4609 values): W1[64][5], b1[64], W2[64][64],
+b2[64], w3[64], b3.  Input: five rotation-invariant, dimensionless features of a
+cell's conserved state; output: W/U (W = rho h G^2), so the guess is W0 = U * y.
+Loss: mean squared error of y against the converged W/U.
+
+bf16=True rounds, as the GPU does, the operands of the three products that run on
+tensor cores to bfloat16 (round to nearest even): h1 and W2 in the forward layer-2
+product, dz2 and h1 in the W2 gradient, dz2 and W2 in the h1 gradient.  Everything
+else is FP64.
+"""
+import numpy as np
+
+NIN, NH = 5, 64
+SIZES = [("W1", (NH, NIN)), ("b1", (NH,)), ("W2", (NH, NH)), ("b2", (NH,)), ("w3", (NH,)),
+         ("b3", (1,))]
+NPARAM = sum(int(np.prod(s)) for _, s in SIZES)
+
+
+def unpack(theta):
+    out, o = {}, 0
+    for name, shape in SIZES:
+        m = int(np.prod(shape))
+        out[name] = np.asarray(theta[o:o + m], dtype=np.float64).reshape(shape)
+        o += m
+    return out
+
+
+def pack(p):
+    return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SIZES])
+
+
+def init(seed):
+    """Glorot-uniform weights, zero biases, as float32 (what the GPU trains)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = {}
+    for name, shape in SIZES:
+        if name.startswith("W") or name == "w3":
+            fan_in = shape[1] if len(shape) == 2 else NH
+            fan_out = shape[0] if len(shape) == 2 else 1
+            lim = np.sqrt(6.0 / (fan_in + fan_out))
+            p[name] = rng.uniform(-lim, lim, shape)
+        else:
+            p[name] = np.zeros(shape)
+    return pack(p).astype(np.float32)
+
+
+def bf16(x):
+    """Round to bfloat16 (nearest even) and back to float64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def features(u, B):
+    """u[5, n] = D, Sx, Sy, Sz, U; B[3, n] cell-centred field -> x[n, 5]:
+    D/U, S^2/U^2, B^2/U, (S.B)^2/(S^2 B^2) (0 when S or B vanish), ln(U/D)."""
+    D, S, U = u[0], u[1:4], u[4]
+    S2 = np.sum(S * S, axis=0)
+    B2 = np.sum(B * B, axis=0)
+    SB = np.sum(S * B, axis=0)
+    den = S2 * B2
+    cos2 = np.where(den > 0, SB * SB / np.where(den > 0, den, 1.0), 0.0)
+    return np.stack([D / U, S2 / (U * U), B2 / U, cos2, np.log(U / D)], axis=1)
+
+
+def forward(theta, x, bf=False):
+    p = unpack(theta)
+    r = bf16 if bf else (lambda a: a)
+    z1 = x @ p["W1"].T + p["b1"]
+    h1 = np.tanh(z1)
+    z2 = r(h1) @ r(p["W2"]).T + p["b2"]
+    h2 = np.tanh(z2)
+    y = h2 @ p["w3"] + p["b3"][0]
+    return y, (x, z1, h1, z2, h2)
+
+
+def loss_grad(theta, x, t, bf=False):
+    """Mean squared error and its gradient (flat, like theta)."""
+    p = unpack(theta)
+    r = bf16 if bf else (lambda a: a)
+    y, (x, z1, h1, z2, h2) = forward(theta, x, bf)
+    B = x.shape[0]
+    loss = np.mean((y - t) ** 2)
+    dy = 2.0 * (y - t) / B
+    g = {"w3": h2.T @ dy, "b3": np.array([np.sum(dy)])}
+    dz2 = np.outer(dy, p["w3"]) * (1.0 - h2 * h2)
+    g["b2"] = dz2.sum(axis=0)
+    g["W2"] = r(dz2).T @ r(h1)
+    dh1 = r(dz2) @ r(p["W2"])
+    dz1 = dh1 * (1.0 - h1 * h1)
+    g["b1"] = dz1.sum(axis=0)
+    g["W1"] = dz1.T @ x
+    return loss, pack(g)

@@ -14,7 +14,8 @@ namespace {
 
 const char *kKernelNames[ECHO_NKERNELS] = {
     "int_c2p", "flux_x", "flux_y", "flux_z", "der_x", "der_y", "der_z", "uct_x",
-    "uct_y", "uct_z", "rk_curl", "dt", "curl", "init", "diag", "misc"};
+    "uct_y", "uct_z", "rk_curl", "dt", "curl", "init", "diag", "misc", "mlp_guess",
+    "unused17", "unused18", "unused19"};
 
 char g_err[256] = "no error";
 
@@ -290,9 +291,38 @@ echo_status echo_set_state(echo_ctx *c, const double *prim, const double *bface,
     return ECHO_OK;
 }
 
-echo_status echo_step(echo_ctx *c, int max_steps, double t_end, int *steps_done, double *t_now)
+}  // extern "C"
+
+// harvest of (features, W/U) after every inversion, for echo_mlp_harvest
+struct Harvest {
+    long stride, capacity;
+    float *feats, *target;
+    unsigned long long *count;
+    long calls;
+};
+
+namespace {
+
+template <typename R>
+void launch_stage(echo_ctx *c, int stage, long idx, Harvest *hv)
 {
-    if (!c) return fail(nullptr, ECHO_ERR_ARG, "ctx is NULL");
+    if (c->cfg.c2p_guess == ECHO_GUESS_MLP && c->mlp_w && c->guess) echo::launch_mlp_guess(c);
+    Path<R>::int_c2p(c, stage, idx, 1);
+    if (hv) {
+        long off = (hv->calls * 7919L) % hv->stride;
+        echo::launch_mlp_harvest(c, hv->stride, off, hv->feats, hv->target, hv->capacity,
+                                 hv->count);
+        hv->calls++;
+    }
+    Path<R>::sweeps(c, stage == 1);
+    if (stage == 1) echo::launch_dt(c);
+    Path<R>::uct(c);
+    Path<R>::rk(c, stage);
+}
+
+echo_status run_steps(echo_ctx *c, int max_steps, double t_end, int *steps_done, double *t_now,
+                      Harvest *hv)
+{
     if (!c->has_state) return fail(c, ECHO_ERR_STATE, "echo_step before echo_set_state");
     if (max_steps < 0) return fail(c, ECHO_ERR_ARG, "max_steps < 0");
     echo_status st = select_device(c);
@@ -309,19 +339,8 @@ echo_status echo_step(echo_ctx *c, int max_steps, double t_end, int *steps_done,
     for (int s = 0; s < max_steps; s++) {
         const long idx = step0 + s;
         for (int stage = 1; stage <= 3; stage++) {
-            if (c->mixed) {
-                Path<float>::int_c2p(c, stage, idx, 1);
-                Path<float>::sweeps(c, stage == 1);
-                if (stage == 1) echo::launch_dt(c);
-                Path<float>::uct(c);
-                Path<float>::rk(c, stage);
-            } else {
-                Path<double>::int_c2p(c, stage, idx, 1);
-                Path<double>::sweeps(c, stage == 1);
-                if (stage == 1) echo::launch_dt(c);
-                Path<double>::uct(c);
-                Path<double>::rk(c, stage);
-            }
+            if (c->mixed) launch_stage<float>(c, stage, idx, hv);
+            else launch_stage<double>(c, stage, idx, hv);
         }
         if (finite_end) {
             if ((st = read_sc(c, &h))) return st;
@@ -346,6 +365,39 @@ echo_status echo_step(echo_ctx *c, int max_steps, double t_end, int *steps_done,
     if (steps_done) *steps_done = (int)(h.step - step0);
     if (t_now) *t_now = h.t;
     return ret;
+}
+
+}  // namespace
+
+extern "C" {
+
+echo_status echo_step(echo_ctx *c, int max_steps, double t_end, int *steps_done, double *t_now)
+{
+    if (!c) return fail(nullptr, ECHO_ERR_ARG, "ctx is NULL");
+    return run_steps(c, max_steps, t_end, steps_done, t_now, nullptr);
+}
+
+echo_status echo_mlp_harvest(echo_ctx *c, int nsteps, long stride, float *feats, float *target,
+                             long capacity, long *count)
+{
+    if (!c) return fail(nullptr, ECHO_ERR_ARG, "ctx is NULL");
+    if (!feats || !target || stride < 1 || capacity < 1)
+        return fail(c, ECHO_ERR_ARG, "echo_mlp_harvest: bad buffers, stride or capacity");
+    echo_status st = select_device(c);
+    if (st) return st;
+    Harvest hv{stride, capacity, feats, target, nullptr, 0};
+    if (cudaMalloc((void **)&hv.count, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, ECHO_ERR_OOM, "echo_mlp_harvest: counter");
+    }
+    cudaMemsetAsync(hv.count, 0, sizeof(unsigned long long), c->stream);
+    st = run_steps(c, nsteps, INFINITY, nullptr, nullptr, &hv);
+    unsigned long long cnt = 0;
+    cudaMemcpyAsync(&cnt, hv.count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(hv.count);
+    if (count) *count = (long)(cnt < (unsigned long long)capacity ? cnt : capacity);
+    return st;
 }
 
 echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *amax, int ptr_kind)

@@ -13,7 +13,7 @@ namespace echo {
 // kernel kinds for launch counting and event timing
 enum Kind {
     K_C2P = 0, K_FLUX_X, K_FLUX_Y, K_FLUX_Z, K_DER_X, K_DER_Y, K_DER_Z,
-    K_UCT_X, K_UCT_Y, K_UCT_Z, K_RK, K_DT, K_CURL, K_INIT, K_DIAG, K_MISC
+    K_UCT_X, K_UCT_Y, K_UCT_Z, K_RK, K_DT, K_CURL, K_INIT, K_DIAG, K_MISC, K_MLP
 };
 
 struct ProfRec {
@@ -115,5 +115,9 @@ void launch_w_from_cold(echo_ctx *c);
 double probe_fma_peak(echo_ctx *c, int fp64);
 // error text of calls without a context (returned by echo_last_error(NULL))
 void set_global_error(const char *msg);
+// learned guess: W0 for every cell into c->guess; harvest of training states
+void launch_mlp_guess(echo_ctx *c);
+void launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,
+                        long capacity, unsigned long long *count);
 
 }  // namespace echo

@@ -18,7 +18,7 @@ ECHO_ERR_C2P, ECHO_ERR_NONFINITE, ECHO_ERR_STATE = -4, -5, -6
 PTR_HOST, PTR_DEVICE = 0, 1
 FP64, MIXED = 0, 1
 GUESS_PREV, GUESS_COLD, GUESS_MLP = 0, 1, 2
-NKERNELS = 16
+NKERNELS = 20
 
 _STATUS = {0: "ECHO_OK", -1: "ECHO_ERR_ARG", -2: "ECHO_ERR_CUDA", -3: "ECHO_ERR_OOM",
            -4: "ECHO_ERR_C2P", -5: "ECHO_ERR_NONFINITE", -6: "ECHO_ERR_STATE"}
@@ -28,7 +28,9 @@ EXPORTS = ["echo_config_default", "echo_create", "echo_destroy", "echo_set_state
            "echo_step", "echo_rhs", "echo_get_primitives", "echo_get_state",
            "echo_set_conserved", "echo_diagnostics", "echo_l1_error", "echo_profile_enable",
            "echo_profile_read", "echo_launches", "echo_probe_fma_peak", "echo_stream",
-           "echo_last_error", "echo_diagnostics_noalloc"]
+           "echo_last_error", "echo_diagnostics_noalloc", "echo_mlp_load", "echo_mlp_forward",
+           "echo_mlp_grad", "echo_mlp_train", "echo_mlp_harvest"]
+MLP_NPARAM = 4609
 
 
 class EchoError(RuntimeError):
@@ -45,6 +47,12 @@ class Config(C.Structure):
                 ("precision", C.c_int), ("c2p_guess", C.c_int),
                 ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
                 ("device", C.c_int), ("stream", C.c_void_p)]
+
+
+class TrainCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("lr_decay", C.c_double), ("seed", C.c_ulong)]
 
 
 class Diag(C.Structure):
@@ -98,6 +106,12 @@ def lib():
     L.echo_last_error.restype = C.c_char_p
     L.echo_diagnostics_noalloc.argtypes = [vp, vp, ip, ip, ip, C.c_double, C.c_double,
                                            C.c_double, ip, vp, vp, ip]
+    fp = C.POINTER(C.c_float)
+    L.echo_mlp_load.argtypes = [vp, fp, C.c_long]
+    L.echo_mlp_forward.argtypes = [fp, vp, C.c_long, vp, vp]
+    L.echo_mlp_grad.argtypes = [fp, vp, vp, C.c_long, fp, fp, vp]
+    L.echo_mlp_train.argtypes = [vp, vp, C.c_long, C.POINTER(TrainCfg), fp, fp, vp]
+    L.echo_mlp_harvest.argtypes = [vp, ip, C.c_long, vp, vp, C.c_long, C.POINTER(C.c_long)]
     _lib = L
     return L
 
@@ -291,3 +305,93 @@ class Solver:
     @property
     def stream(self):
         return self.L.echo_stream(self._h)
+
+
+# ---------------------------------------------------------------------------
+# the learned Newton starting guess
+# ---------------------------------------------------------------------------
+
+def _f32(w):
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+    if w.size != MLP_NPARAM:
+        raise ValueError("need %d parameters" % MLP_NPARAM)
+    return w
+
+
+def _dev_f32(t, what, count):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == count):
+        raise ValueError("%s: need a contiguous float32 CUDA tensor of %d elements" % (what, count))
+    return C.c_void_p(t.data_ptr())
+
+
+def _chk(st, what):
+    if st != ECHO_OK:
+        raise EchoError(st, "%s: %s" % (what, lib().echo_last_error(None).decode()))
+
+
+def mlp_forward(weights, feats):
+    """y[n] (torch CUDA float32) for feats[n, 5] (torch CUDA float32)."""
+    import torch
+    n = feats.shape[0]
+    y = torch.empty(n, dtype=torch.float32, device=feats.device)
+    w = _f32(weights)
+    torch.cuda.synchronize()
+    _chk(lib().echo_mlp_forward(w.ctypes.data_as(C.POINTER(C.c_float)),
+                                _dev_f32(feats, "feats", 5 * n), n, C.c_void_p(y.data_ptr()), None),
+         "echo_mlp_forward")
+    return y
+
+
+def mlp_grad(weights, feats, target):
+    """(mean squared loss, gradient[4609]) for one batch (n a multiple of 64)."""
+    import torch
+    n = feats.shape[0]
+    w = _f32(weights)
+    g = np.zeros(MLP_NPARAM, dtype=np.float32)
+    loss = C.c_float()
+    torch.cuda.synchronize()
+    fp = C.POINTER(C.c_float)
+    _chk(lib().echo_mlp_grad(w.ctypes.data_as(fp), _dev_f32(feats, "feats", 5 * n),
+                             _dev_f32(target, "target", n), n, g.ctypes.data_as(fp),
+                             C.byref(loss), None), "echo_mlp_grad")
+    return loss.value, g
+
+
+def mlp_train(feats, target, weights, epochs=5, batch=1024, lr=2e-3, beta1=0.9, beta2=0.999,
+              eps=1e-8, lr_decay=0.7, seed=0):
+    """Adam on the GPU; returns (trained weights, mean loss per epoch)."""
+    import torch
+    n = feats.shape[0]
+    w = _f32(weights).copy()
+    hist = np.zeros(epochs, dtype=np.float32)
+    cfg = TrainCfg(epochs, batch, lr, beta1, beta2, eps, lr_decay, seed)
+    torch.cuda.synchronize()
+    fp = C.POINTER(C.c_float)
+    _chk(lib().echo_mlp_train(_dev_f32(feats, "feats", 5 * n), _dev_f32(target, "target", n), n,
+                              C.byref(cfg), w.ctypes.data_as(fp), hist.ctypes.data_as(fp), None),
+         "echo_mlp_train")
+    return w, hist
+
+
+def _solver_mlp_load(self, weights):
+    w = _f32(weights)
+    self._check(self.L.echo_mlp_load(self._h, w.ctypes.data_as(C.POINTER(C.c_float)),
+                                     MLP_NPARAM))
+
+
+def _solver_mlp_harvest(self, nsteps, stride, feats, target):
+    """Advance nsteps steps, collecting features and W/U after every inversion
+    into feats[cap, 5], target[cap] (torch CUDA float32); returns the count."""
+    import torch
+    cap = target.shape[0]
+    cnt = C.c_long()
+    torch.cuda.synchronize()
+    self._check(self.L.echo_mlp_harvest(self._h, nsteps, stride,
+                                        _dev_f32(feats, "feats", 5 * cap),
+                                        _dev_f32(target, "target", cap), cap, C.byref(cnt)))
+    return cnt.value
+
+
+Solver.mlp_load = _solver_mlp_load
+Solver.mlp_harvest = _solver_mlp_harvest

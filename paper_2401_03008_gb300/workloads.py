@@ -203,3 +203,118 @@ def random_smooth_fields(nx, ny, nz, seed, amp=0.3, kmax=2, L=(1.0, 1.0, 1.0),
     for c in range(3):
         apot[c] = amp * field(offs[c], 1.0) / (2 * math.pi)
     return prim, bg, apot
+
+
+# ---------------------------------------------------------------------------
+# Decaying relativistic Alfvenic turbulence (3-D extension of the Sec. 5 set-up)
+# ---------------------------------------------------------------------------
+
+def _modes(kmax):
+    """Integer wave vectors with 1 <= |k| <= kmax, one of each +-k pair."""
+    out = []
+    r = int(kmax)
+    for kz in range(-r, r + 1):
+        for ky in range(-r, r + 1):
+            for kx in range(0, r + 1):
+                k2 = kx * kx + ky * ky + kz * kz
+                if k2 == 0 or k2 > kmax * kmax:
+                    continue
+                # half space: kx > 0, or kx == 0 and (ky > 0, or ky == 0 and kz > 0)
+                if kx == 0 and (ky < 0 or (ky == 0 and kz < 0)):
+                    continue
+                out.append((kx, ky, kz))
+    return np.array(out, dtype=np.float64)
+
+
+def _synth(n, modes, coef, phase, off):
+    """Real periodic field sum_m coef[m] cos(k_m . x + phase[m]) on an n^3 grid of a
+    2 pi box, sampled at (i + off) h per axis (h = 2 pi / n), by inverse real FFT
+    (exact for integer wave vectors).  Returns [nz, ny, nx]."""
+    spec = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    h = 2.0 * np.pi / n
+    for m, k in enumerate(modes):
+        kx, ky, kz = (int(round(q)) for q in k)
+        shift = (kx * off[0] + ky * off[1] + kz * off[2]) * h
+        c = coef[m] * np.exp(1j * (phase[m] + shift)) * n ** 3
+        if kx > 0:
+            spec[kz % n, ky % n, kx] += c
+        else:  # kx = 0 plane: put both members of the pair (irfftn needs Hermitian input)
+            spec[kz % n, ky % n, 0] += 0.5 * c
+            spec[(-kz) % n, (-ky) % n, 0] += 0.5 * np.conj(c)
+    return np.fft.irfftn(spec, s=(n, n, n), axes=(0, 1, 2))
+
+
+class Turbulence:
+    """3-D decaying relativistic Alfvenic turbulence on a periodic (2 pi)^3 box.
+
+    Background (Sec. 5 with the magnetisation of the 3-D benchmark): rho0 = 1, a
+    uniform field B0 along z with sigma0 = B0^2/rho0 (default 10) and
+    beta0 = 2 p0/B0^2 = 1, at rest.  Fluctuations: all integer modes with
+    1 <= |k| <= kmax (default 4), random phases and random unit vectors e(k)
+    perpendicular to k, independent for the velocity and the field (Sec. 5 uses
+    different phases for v and B), so both are divergence-free:
+      delta B = curl A,  A = sum_k (a_B/|k|) e_B(k) sin(k.x + phi_B(k)),
+      u = sum_k a_u (k x e_u(k))/|k| cos(k.x + phi_u(k))  (a 4-velocity),
+      v = u / sqrt(1 + u^2).
+    The amplitudes are set afterwards (as in Sec. 5): a_B so that the mean of
+    |delta B| over the cell centres is eta_b B0, a_u so that the largest Lorentz
+    factor on the grid is lorentz_max.  Seeded (PCG64)."""
+
+    def __init__(self, n, seed, sigma0=10.0, beta0=1.0, rho0=1.0, eta_b=0.5, lorentz_max=5.0,
+                 kmax=4.0, gam=GAMMA):
+        self.n = n
+        self.L = (2 * np.pi,) * 3
+        self.rho0, self.gam = rho0, gam
+        self.B0 = math.sqrt(sigma0 * rho0)
+        self.p0 = 0.5 * beta0 * self.B0 ** 2
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.modes = _modes(kmax)
+        nm = len(self.modes)
+        kn = np.linalg.norm(self.modes, axis=1)
+
+        def perp_units():
+            e = rng.normal(size=(nm, 3))
+            e -= (np.sum(e * self.modes, axis=1) / kn ** 2)[:, None] * self.modes
+            return e / np.linalg.norm(e, axis=1)[:, None]
+
+        self.eB = perp_units()
+        self.phB = rng.uniform(0, 2 * np.pi, nm)
+        self.eu = perp_units()
+        self.phu = rng.uniform(0, 2 * np.pi, nm)
+        kxe_B = np.cross(self.modes, self.eB) / kn[:, None]   # unit vectors (e perp k)
+        kxe_u = np.cross(self.modes, self.eu) / kn[:, None]
+        self._kn = kn
+        # unit-amplitude delta B and u at cell centres, for the normalisation
+        c = (0.5, 0.5, 0.5)
+        dB = np.array([_synth(n, self.modes, kxe_B[:, q], self.phB, c) for q in range(3)])
+        self.aB = eta_b * self.B0 / np.mean(np.sqrt(np.sum(dB ** 2, axis=0)))
+        u = np.array([_synth(n, self.modes, kxe_u[:, q], self.phu, c) for q in range(3)])
+        umax = np.max(np.sqrt(np.sum(u ** 2, axis=0)))
+        self.au = math.sqrt(lorentz_max ** 2 - 1.0) / umax
+        u *= self.au
+        self._v = u / np.sqrt(1.0 + np.sum(u ** 2, axis=0))[None]
+
+    def prim5(self):
+        n = self.n
+        out = np.empty((5, n, n, n))
+        out[0] = self.rho0
+        out[1:4] = self._v
+        out[4] = self.p0
+        return out
+
+    def bface_background(self):
+        n = self.n
+        out = np.zeros((3, n, n, n))
+        out[2] = self.B0
+        return out
+
+    def apot(self):
+        """Edge vector potential: A_x at (i, j+1/2, k+1/2) and cyclic."""
+        n = self.n
+        offs = [(0.5, 1.0, 1.0), (1.0, 0.5, 1.0), (1.0, 1.0, 0.5)]
+        out = np.empty((3, n, n, n))
+        for c in range(3):
+            # sin(k.x + phi) = cos(k.x + phi - pi/2)
+            coef = self.aB / self._kn * self.eB[:, c]
+            out[c] = _synth(n, self.modes, coef, self.phB - 0.5 * np.pi, offs[c])
+        return out

@@ -1,0 +1,69 @@
+"""Pins of the MLP oracle: backpropagation against finite differences, the bfloat16
+rounding against torch, and the invariances the features must have."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from oracle import oracle as orc
+from paper_2401_03008_gb300 import workloads as wl
+
+
+def _batch(n, seed):
+    prim, B = wl.random_states(n, seed=seed, lorentz_max=5.0, sigma_max=20.0)
+    u = np.array([orc.prim2cons(prim[:, q], B[:, q], 4 / 3) for q in range(n)]).T
+    v2 = np.sum(prim[1:4] ** 2, axis=0)
+    W = (prim[0] + 4 * prim[4]) / (1 - v2)
+    return u, B, W
+
+
+def test_gradient_matches_finite_differences():
+    u, B, W = _batch(40, 51)
+    x = mlp.features(u, B)
+    t = W / u[4]
+    theta = mlp.init(52).astype(np.float64)
+    loss, g = mlp.loss_grad(theta, x, t)
+    rng = np.random.default_rng(53)
+    for i in rng.choice(mlp.NPARAM, 60, replace=False).tolist() + [mlp.NPARAM - 1, 0]:
+        e = np.zeros(mlp.NPARAM)
+        h = 1e-6
+        e[i] = h
+        lp, _ = mlp.loss_grad(theta + e, x, t)
+        lm, _ = mlp.loss_grad(theta - e, x, t)
+        fd = (lp - lm) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-10), i
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(54)
+    x = np.concatenate([rng.normal(size=5000) * 10.0 ** rng.uniform(-8, 8, 5000),
+                        np.array([0.0, -0.0, 1.0, 1.00390625, 1.01171875, 65504.0])])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16(x), ref)
+
+
+def test_features_invariant_under_rotation_and_scaling():
+    u, B, W = _batch(50, 55)
+    x = mlp.features(u, B)
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    u2 = u.copy()
+    u2[1:4] = R @ u[1:4]
+    B2 = R @ B
+    assert np.allclose(mlp.features(u2, B2), x, rtol=1e-12, atol=1e-14)
+    # energy densities scale by lam, B by sqrt(lam): the features do not change
+    lam = 3.7
+    u3 = u * lam
+    assert np.allclose(mlp.features(u3, B * np.sqrt(lam)), x, rtol=1e-12, atol=1e-14)
+    assert np.all((x[:, 3] >= 0) & (x[:, 3] <= 1)) and np.all(x[:, 0] > 0)
+
+
+def test_bf16_emulation_is_close_to_fp64():
+    u, B, W = _batch(256, 56)
+    x = mlp.features(u, B)
+    t = W / u[4]
+    theta = mlp.init(57).astype(np.float64)
+    l64, g64 = mlp.loss_grad(theta, x, t)
+    lbf, gbf = mlp.loss_grad(theta, x, t, bf=True)
+    assert abs(lbf - l64) / l64 < 1e-2
+    assert np.linalg.norm(gbf - g64) / np.linalg.norm(g64) < 2e-2
