@@ -185,10 +185,17 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variants", type=int, default=1, help="also time mixed and mixed+learned")
+    ap.add_argument("--config", type=int, default=0, help="run benchmark-plan configuration 1..5")
+    ap.add_argument("--config-steps", type=int, default=20)
+    ap.add_argument("--config5-n", type=int, default=768)
+    ap.add_argument("--config5-fp64-steps", type=int, default=5)
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.config:
+        return run_config(args)
 
     import torch
     from paper_2401_03008_gb300 import echo
@@ -235,6 +242,8 @@ def main():
         ms = float(tt.item())
     value = world * n ** 3 * args.steps / (ms * 1e-3)
     diag = s.diagnostics()
+    # FP64 state after warm-up + timed steps: the variants are compared with it
+    ref = s.primitives() if (args.variants and args.precision == "fp64") else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -247,6 +256,8 @@ def main():
                     "c2p_failures": diag["c2p_failures"]}}
     if args.prof_steps > 0:
         out.update(roofline_and_profile(args, s, n))
+    if ref is not None:
+        out["variants"] = variants(args, n, st, ref, stream)
     if not args.no_e2e:
         out["e2e"] = end_to_end(args, s, n, world)
     if rank == 0 and not args.no_cpu:
@@ -312,6 +323,188 @@ def roofline_and_profile(args, s, n):
     return {"roofline": roof, "kernel_ms_per_step":
             {k: v[1] / args.prof_steps for k, v in sorted(prof.items())},
             "measured_vector_peaks_tflops": {"fp64": fp64_peak / 1e12, "fp32": fp32_peak / 1e12}}
+
+
+def l1_rel(p, ref):
+    """L1 distance per primitive, normalised by the field scale (max |.| of rho, of
+    the three velocity components together, of p, of the three field components)."""
+    import numpy as np
+    out = []
+    for grp in ([0], [1, 2, 3], [4], [5, 6, 7]):
+        scale = float(np.max(np.abs(ref[grp])))
+        for v in grp:
+            out.append(float(np.mean(np.abs(p[v] - ref[v]))) / scale)
+    return out
+
+
+def harvest_and_train(n_h, steps, stride, make_state, L, seed, epochs=4, cap=None):
+    """Learned guess trained on states the solver produced: harvest (features, W/U)
+    from a run of the same workload family, train on the GPU."""
+    import torch
+    from paper_2401_03008_gb300 import echo
+    from paper_2401_03008_gb300 import workloads as wl
+    cap = cap or steps * 3 * n_h ** 3 // stride + 1
+    h = echo.Solver(n_h, n_h, n_h, L=L)
+    h.set_state(*make_state(n_h))
+    feats = torch.empty((cap, 5), dtype=torch.float32, device="cuda")
+    target = torch.empty(cap, dtype=torch.float32, device="cuda")
+    cnt = h.mlp_harvest(steps, stride, feats, target)
+    h.close()
+    t0 = time.perf_counter()
+    w, hist = echo.mlp_train(feats[:cnt].contiguous(), target[:cnt].contiguous(), wl.mlp_init(seed),
+                             epochs=epochs, batch=4096, lr=3e-3, lr_decay=0.6)
+    torch.cuda.synchronize()
+    return w, {"states": int(cnt), "epochs": epochs, "train_s": time.perf_counter() - t0,
+               "loss_first": float(hist[0]), "loss_last": float(hist[-1])}
+
+
+def run_variant(n, L, st, precision, guess, steps, warmup, stream, weights=None):
+    import torch
+    from paper_2401_03008_gb300 import echo
+    v = echo.Solver(n, n, n, L=L, precision=precision, guess=guess, stream=stream.cuda_stream)
+    if weights is not None:
+        v.mlp_load(weights)
+    v.set_state(*st)
+    v.step(warmup)
+    v.diagnostics(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    v.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    d = v.diagnostics()
+    p = v.primitives()
+    v.close()
+    return {"value": n ** 3 * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "newton_it_fp64": d["newton_it_mean"], "newton_it_fp32": d["newton_it32_mean"],
+            "c2p_fallback_rate": d["c2p_fallbacks"] / max(d["c2p_calls"], 1),
+            "c2p_failures": d["c2p_failures"]}, p
+
+
+def variants(args, n, st, ref, stream):
+    """The mixed path and the mixed path with the learned guess on the same workload
+    and step count as the headline, with their L1 distance to the FP64 result."""
+    L = (1.0, 1.0, 1.0)
+    out = {}
+    r, p = run_variant(n, L, st, "mixed", "prev", args.steps, args.warmup, stream)
+    r["l1_vs_fp64"] = l1_rel(p, ref)
+    out["mixed"] = r
+    mk = lambda m: workload_state(m, args.wave)[1]
+    w, info = harvest_and_train(64, 8, 4, mk, L, 2401030081)
+    r, p = run_variant(n, L, st, "mixed", "mlp", args.steps, args.warmup, stream, w)
+    r["l1_vs_fp64"] = l1_rel(p, ref)
+    r["training"] = info
+    out["mixed_mlp"] = r
+    return out
+
+
+def run_config(args):
+    """The five configurations of the benchmark plan, one JSON line each (for the
+    design notes; the default run is the headline line)."""
+    import numpy as np
+    import torch
+    from paper_2401_03008_gb300 import echo
+    from paper_2401_03008_gb300 import workloads as wl
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def timed(sol, steps, t_end=math.inf):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        done, t = sol.step(steps, t_end)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return done, t, e0.elapsed_time(e1)
+
+    out = {"config": args.config}
+    if args.config == 1:
+        from oracle import oracle as orc
+        n = 32
+        c = wl.CPA(n, n, n, m=(1, 0, 0))
+        st = (c.prim5(), c.bface_background(), c.apot())
+        s = echo.Solver(n, n, n, stream=sp)
+        s.set_state(*st)
+        done, t, ms = timed(s, 20)
+        g = orc.Grid(n, n, n, nthreads=os.cpu_count())
+        g.set_state(*st)
+        t0 = time.perf_counter()
+        g.step(20)
+        el = time.perf_counter() - t0
+        p, ref = s.primitives(), g.primitives()
+        rel = []
+        for grp in ([0], [1, 2, 3], [4], [5, 6, 7]):
+            sc = np.max(np.abs(ref[grp]))
+            rel += [float(np.max(np.abs(p[v] - ref[v])) / sc) for v in grp]
+        out.update({"workload": "Alfven wave along x, 32^3, FP64, 20 steps", "steps": done,
+                    "t": t, "gpu_cell_updates_per_s": n ** 3 * 20 / (ms * 1e-3),
+                    "oracle_cell_updates_per_s": n ** 3 * 20 / el, "oracle_threads": os.cpu_count(),
+                    "max_rel_diff_vs_oracle": rel,
+                    "l1_vs_exact": list(map(float, s.l1_error(c.exact_prim8(t))))})
+    elif args.config in (2, 3):
+        n = 256 if args.config == 2 else 512
+        c = wl.CPA(n, n, n, m=(1, 1, 1))
+        st = (c.prim5(), c.bface_background(), c.apot())
+        res = {}
+        precs = ["fp64"] if args.config == 2 else ["fp64", "mixed"]
+        prims = {}
+        for prec in precs:
+            s = echo.Solver(n, n, n, precision=prec, stream=sp)
+            s.set_state(*st)
+            if args.config == 2:
+                done, t, ms = timed(s, 100000, c.period)
+            else:
+                done, t, ms = timed(s, args.config_steps)
+            d = s.diagnostics()
+            ex = c.exact_prim8(t)
+            res[prec] = {"steps": done, "t": t, "cell_updates_per_s": n ** 3 * done / (ms * 1e-3),
+                         "ms_per_step": ms / done, "l1_vs_exact": list(map(float, s.l1_error(ex))),
+                         "divb_max": d["divb_max"], "newton_it_fp64": d["newton_it_mean"],
+                         "newton_it_fp32": d["newton_it32_mean"], "c2p_failures": d["c2p_failures"]}
+            prims[prec] = s.primitives()
+            s.close()
+        if args.config == 3:
+            res["mixed"]["l1_vs_fp64"] = l1_rel(prims["mixed"], prims["fp64"])
+        out.update({"workload": "Alfven wave along (1,1,1), %d^3" % n
+                    + (", one period" if args.config == 2 else ", %d steps" % args.config_steps),
+                    "period": c.period, "results": res})
+    else:
+        n = 512 if args.config == 4 else args.config5_n
+        L = (2 * np.pi,) * 3
+        seed = 2401_03008
+        tb = wl.Turbulence(n, seed=seed, lorentz_max=2.0)
+        st = (tb.prim5(), tb.bface_background(), tb.apot())
+        mk = lambda m: (lambda t: (t.prim5(), t.bface_background(), t.apot()))(
+            wl.Turbulence(m, seed=seed + 1, lorentz_max=2.0))
+        # 1e7 training states from 128^3 runs of another seed
+        w, info = harvest_and_train(128, 20, 4, mk, L, seed + 2, epochs=4, cap=10_000_000)
+        res = {"training": info}
+        runs = ([("fp64", "prev"), ("fp64", "cold"), ("fp64", "mlp"), ("mixed", "prev"),
+                 ("mixed", "cold"), ("mixed", "mlp")] if args.config == 4 else
+                [("fp64", "prev"), ("mixed", "mlp"), ("mixed", "prev")])
+        prims = {}
+        for prec, guess in runs:
+            steps = args.config_steps if prec == "mixed" or args.config == 4 else args.config5_fp64_steps
+            r, p = run_variant(n, L, st, prec, guess, steps, 1, stream,
+                               w if guess == "mlp" else None)
+            r["steps"] = steps
+            res["%s_%s" % (prec, guess)] = r
+            prims[(prec, guess)] = p
+        if args.config == 5:
+            # the mixed runs and the FP64 run may differ in step count: compare the
+            # mixed variants with each other and report the FP64 rate
+            res["mixed_mlp"]["l1_vs_mixed_prev"] = l1_rel(prims[("mixed", "mlp")], prims[("mixed", "prev")])
+        else:
+            res["mixed_prev"]["l1_vs_fp64_prev"] = l1_rel(prims[("mixed", "prev")], prims[("fp64", "prev")])
+            res["mixed_mlp"]["l1_vs_fp64_prev"] = l1_rel(prims[("mixed", "mlp")], prims[("fp64", "prev")])
+        out.update({"workload": "decaying Alfvenic turbulence, %d^3, sigma0 = 10, beta0 = 1, "
+                                "mean |dB|/B0 = 0.5, max Lorentz factor 2, |k| <= 4, seed %d"
+                                % (n, seed), "results": res})
+    print(json.dumps(out))
 
 
 def end_to_end(args, s, n, world):

@@ -58,7 +58,9 @@ enum { ECHO_REC_MP5 = 0 };
 /* ECHO_FP64: every step in double precision.  ECHO_MIXED: reconstruction, fluxes,
  * HLL, DER and the UCT fields in single precision; the inversion (Lorentz factor and
  * pressure recovery included) and the Runge-Kutta accumulation of the conserved
- * state in double precision. */
+ * state in double precision.  The mixed path refines each Newton starting guess
+ * with FP32 iterations before the FP64 ones; the FP64 iteration and its stopping
+ * rule decide the result. */
 enum { ECHO_FP64 = 0, ECHO_MIXED = 1 };
 /* Newton starting guess: W of the previous call at the same cell, W0 = U, or the
  * small learned network loaded with echo_mlp_load (falls back to the previous W
@@ -75,14 +77,14 @@ typedef struct {
     int rec;            /* ECHO_REC_MP5 */
     int precision;      /* ECHO_FP64 or ECHO_MIXED */
     int c2p_guess;      /* ECHO_GUESS_* */
-    double c2p_tol;     /* Newton stop |dW| <= tol W, then one polishing step */
+    double c2p_tol;     /* Newton stop: an undamped step |dW| <= tol W, then one polishing step */
     int c2p_maxit;      /* Newton iteration cap (a cell past it is a failure) */
     int device;         /* CUDA device ordinal */
     void *stream;       /* cudaStream_t to launch on; NULL: the library makes one */
 } echo_config;
 
 /* Fill *cfg with defaults: 32^3 unit box, gamma 4/3, cfl 0.4, uct 1, ho 1, MP5,
- * FP64, previous-W guess, tol 1e-12, maxit 100, device 0, own stream. */
+ * FP64, previous-W guess, tol 1e-6, maxit 100, device 0, own stream. */
 echo_status echo_config_default(echo_config *cfg);
 
 /* Validate cfg, select its device, allocate the device state (library-owned) and
@@ -144,11 +146,12 @@ typedef struct {
     double t, dt, amax;        /* time, last dt, largest fast speed of the last step */
     double divb_max, divb_l2;  /* discrete div B (same DER as the curl), max |.| and RMS */
     double tot[8];             /* sums of D, Sx, Sy, Sz, U and face Bx, By, Bz (compensated) */
-    double newton_it_mean;     /* Newton iterations per inversion since the last reset */
+    double newton_it_mean;     /* FP64 Newton iterations per inversion since the last reset */
     int newton_it_max;
     long c2p_calls, c2p_fallbacks, c2p_failures;
     long nonfinite;            /* non-finite values found in the state */
     long step;
+    double newton_it32_mean;   /* FP32 pre-iterations per inversion (mixed path) */
 } echo_diag;
 
 /* Diagnostics of the current state (Sec. 3: div B preserved by UCT; conservation of

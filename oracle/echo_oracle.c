@@ -310,8 +310,9 @@ double orc_der(const double *s, double h, int ho)
  *   p(W)   = (gam-1)/gam [W (1 - v^2) - D sqrt(1 - v^2)],
  * and W solves f(W) = W - p + (1 + v^2) B^2/2 - (S.B)^2/(2 W^2) - U = 0.
  * Newton with the analytic derivative; a trial point outside the domain
- * (W <= 0, v^2 >= 1, not finite) halves the step.  The iteration stops when
- * |dW| <= tol W, after one more polishing step. */
+ * (W <= 0, v^2 >= 1, not finite) halves the step.  The iteration stops after an
+ * undamped step with |dW| <= tol W and one more polishing step (after such a step
+ * the error is about tol^2 W, and the polishing step squares it again). */
 
 typedef struct { double D, S2, B2, SB, U, gm1g; } c2p_inv;
 
@@ -385,7 +386,7 @@ int orc_c2p(const double *u, const double *B, double gam, double W0, double tol,
         double step = fabs(Wn - W);
         W = Wn;
         if (polish) { conv = 1; break; }
-        if (step <= tol * W) polish = 1;
+        if (lam == 1.0 && step <= tol * W) polish = 1;
     }
     *iters = it;
     *W_out = W;

@@ -33,21 +33,6 @@ def pack(p):
     return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SIZES])
 
 
-def init(seed):
-    """Glorot-uniform weights, zero biases, as float32 (what the GPU trains)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    p = {}
-    for name, shape in SIZES:
-        if name.startswith("W") or name == "w3":
-            fan_in = shape[1] if len(shape) == 2 else NH
-            fan_out = shape[0] if len(shape) == 2 else 1
-            lim = np.sqrt(6.0 / (fan_in + fan_out))
-            p[name] = rng.uniform(-lim, lim, shape)
-        else:
-            p[name] = np.zeros(shape)
-    return pack(p).astype(np.float32)
-
-
 def bf16(x):
     """Round to bfloat16 (nearest even) and back to float64."""
     f = np.asarray(x, dtype=np.float32)

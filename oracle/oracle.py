@@ -143,7 +143,7 @@ def c2p_fdf(u, B, gam, W):
     return f.value, df.value
 
 
-def c2p(u, B, gam, W0, tol=1e-12, maxit=100):
+def c2p(u, B, gam, W0, tol=1e-6, maxit=100):
     prim = np.zeros(5)
     W = C.c_double()
     it = C.c_int()
@@ -152,7 +152,7 @@ def c2p(u, B, gam, W0, tol=1e-12, maxit=100):
     return prim, W.value, it.value, bad
 
 
-def c2p_batch(u, B, W0, gam, tol=1e-12, maxit=100):
+def c2p_batch(u, B, W0, gam, tol=1e-6, maxit=100):
     """u[5, n], B[3, n], W0[n] -> prim[5, n], W[n], iterations[n], failures."""
     u = _vec(u)
     B = _vec(B)
@@ -179,7 +179,7 @@ class Grid:
     """Oracle state on a periodic nx*ny*nz grid: cons[5], face (or cell) B[3], W."""
 
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, gam=4.0 / 3.0, cfl=0.4,
-                 uct=1, ho=1, tol=1e-12, maxit=100, guess=GUESS_WARM, nthreads=0):
+                 uct=1, ho=1, tol=1e-6, maxit=100, guess=GUESS_WARM, nthreads=0):
         self.cfg = Cfg(nx, ny, nz, lx, ly, lz, gam, cfl, uct, ho, tol, maxit, guess,
                        nthreads or int(os.environ.get("ORACLE_THREADS", "0")))
         self.shape = (nz, ny, nx)

@@ -109,7 +109,7 @@ void free_all(echo_ctx *c)
 {
     void *ptrs[] = {c->U, c->U0, c->Bf, c->Bf0, c->W, c->prim, c->flux, c->fdat[0], c->fdat[1],
                     c->fdat[2], c->E, c->rhs, c->sc, c->partials, c->dres, c->stage8,
-                    c->mlp_w, c->guess};
+                    c->mlp_w, c->guess, c->Bf32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : c->prof) {
@@ -139,7 +139,7 @@ echo_status echo_config_default(echo_config *cfg)
     cfg->rec = ECHO_REC_MP5;
     cfg->precision = ECHO_FP64;
     cfg->c2p_guess = ECHO_GUESS_PREV;
-    cfg->c2p_tol = 1e-12;
+    cfg->c2p_tol = 1e-6;
     cfg->c2p_maxit = 100;
     cfg->device = 0;
     cfg->stream = nullptr;
@@ -218,8 +218,10 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
         {(void **)&c->sc, sizeof(DevScalars)},
         {(void **)&c->partials, echo::DIAG_BLOCKS * echo::DIAG_Q * sizeof(double)},
         {(void **)&c->dres, 32 * sizeof(double)},
+        {(void **)&c->Bf32, c->mixed ? 3 * n * sizeof(float) : 0},
     };
     for (auto &a : al) {
+        if (a.bytes == 0) continue;
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
             cudaGetLastError();
             *a.p = nullptr;
@@ -277,6 +279,7 @@ echo_status echo_set_state(echo_ctx *c, const double *prim, const double *bface,
     const double *dp;
     if ((st = input(c, prim, 5 * n, ptr_kind, 0, &dp))) return st;
     echo::launch_init(c, dp);
+    echo::launch_bf32(c);
     DevScalars h;
     memset(&h, 0, sizeof(h));
     h.cfl = c->cfg.cfl;
@@ -306,7 +309,6 @@ namespace {
 template <typename R>
 void launch_stage(echo_ctx *c, int stage, long idx, Harvest *hv)
 {
-    if (c->cfg.c2p_guess == ECHO_GUESS_MLP && c->mlp_w && c->guess) echo::launch_mlp_guess(c);
     Path<R>::int_c2p(c, stage, idx, 1);
     if (hv) {
         long off = (hv->calls * 7919L) % hv->stride;
@@ -354,6 +356,7 @@ echo_status run_steps(echo_ctx *c, int max_steps, double t_end, int *steps_done,
         // roll back to the start of the failed step
         if (h.fail_stage >= 2) {
             echo::launch_copy_state(c, c->U, c->Bf, c->U0, c->Bf0);
+            echo::launch_bf32(c);
             h.t = h.t_prev;
         }
         h.halt = 0;
@@ -498,6 +501,7 @@ echo_status echo_set_conserved(echo_ctx *c, const double *cons5, const double *b
     CK(cudaMemcpyAsync(c->Bf, bface, 3 * n * sizeof(double), k, c->stream));
     if (w) CK(cudaMemcpyAsync(c->W, w, n * sizeof(double), k, c->stream));
     else echo::launch_w_from_cold(c);
+    echo::launch_bf32(c);
     DevScalars h;
     if ((st = read_sc(c, &h))) return st;
     memset(&h, 0, sizeof(h));
@@ -532,11 +536,13 @@ echo_status echo_diagnostics(echo_ctx *c, echo_diag *out, int reset_counters)
     out->c2p_calls = (long)h.c2p_calls;
     out->newton_it_mean = h.c2p_calls ? (double)h.it_sum / (double)h.c2p_calls : 0.0;
     out->newton_it_max = (int)h.it_max;
+    out->newton_it32_mean = h.c2p_calls ? (double)h.it32_sum / (double)h.c2p_calls : 0.0;
     out->c2p_fallbacks = h.fallbacks;
     out->c2p_failures = h.fails;
     out->step = h.step;
     if (reset_counters) {
         h.it_sum = 0;
+        h.it32_sum = 0;
         h.c2p_calls = 0;
         h.it_max = 0;
         h.fallbacks = 0;

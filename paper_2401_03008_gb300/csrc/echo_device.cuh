@@ -31,7 +31,8 @@ struct DevScalars {
     double t_prev;                 // time at the start of the step in progress
     double t_end;
     double cfl;
-    unsigned long long it_sum;     // Newton iterations summed
+    unsigned long long it_sum;     // FP64 Newton iterations summed
+    unsigned long long it32_sum;   // FP32 pre-iterations summed (mixed path)
     unsigned long long c2p_calls;
     unsigned int it_max;
     unsigned int fails;            // failed inversions
@@ -48,6 +49,7 @@ struct C2PParams {
     double tol;
     int maxit;
     int guess;  // 0 previous W, 1 W0 = U, 2 learned guess array
+    int pre32;  // mixed path: FP32 Newton iterations refine the guess first
 };
 
 __device__ __forceinline__ int wrapi(int i, int n)
@@ -142,14 +144,21 @@ __device__ __forceinline__ R minmod4(R a, R b, R c, R d)
 
 // MP5 value at i+1/2 from (u_{i-2}, ..., u_{i+2}): fifth-order point-value
 // interpolant (3, -20, 90, 60, -5)/128 bounded by the monotonicity-preserving
-// limiter of Suresh & Huynh (alpha = 4, eps = 1e-10).
+// limiter of Suresh & Huynh (alpha = 4, eps = 1e-10).  Split in two: the smooth
+// candidate with its test, and the limiting that only a few interfaces need.
 template <typename R>
-__device__ __forceinline__ R mp5(R um2, R um1, R u0, R up1, R up2)
+__device__ __forceinline__ bool mp5_smooth(R um2, R um1, R u0, R up1, R up2, R &uor)
 {
     const R alpha = R(4);
-    R uor = (R(3) * um2 - R(20) * um1 + R(90) * u0 + R(60) * up1 - R(5) * up2) * R(0.0078125);
+    uor = (R(3) * um2 - R(20) * um1 + R(90) * u0 + R(60) * up1 - R(5) * up2) * R(0.0078125);
     R ump = u0 + minmod2(up1 - u0, alpha * (u0 - um1));
-    if (le((uor - u0) * (uor - ump), R(1e-10))) return uor;
+    return le((uor - u0) * (uor - ump), R(1e-10));
+}
+
+template <typename R>
+__device__ __forceinline__ R mp5_limit(R um2, R um1, R u0, R up1, R up2, R uor)
+{
+    const R alpha = R(4);
     R djm1 = um2 - R(2) * um1 + u0;
     R dj = um1 - R(2) * u0 + up1;
     R djp1 = u0 - R(2) * up1 + up2;
@@ -163,6 +172,61 @@ __device__ __forceinline__ R mp5(R um2, R um1, R u0, R up1, R up2)
     R umax = rmin(rmax(rmax(u0, up1), umd), rmax(rmax(u0, uul), ulc));
     return uor + minmod2(umin - uor, umax - uor);
 }
+
+template <typename R>
+__device__ __forceinline__ R mp5(R um2, R um1, R u0, R up1, R up2)
+{
+    R uor;
+    if (mp5_smooth(um2, um1, u0, up1, up2, uor)) return uor;
+    return mp5_limit(um2, um1, u0, up1, up2, uor);
+}
+
+// Deferred limiting.  Most interfaces pass the smooth test; the few that do not
+// are scattered over most warps, and limiting them in place would run the
+// limiter with a handful of lanes active.  Instead a thread queues its five
+// stencil values and the candidate in shared memory; after a barrier the whole
+// block limits the queued entries with full warps, and each thread collects its
+// results.  Same arithmetic as mp5(), so the same results.  Entries beyond QMAX
+// are limited in place.
+template <typename R, int NSLOT, int QMAX, int NT>
+struct Mp5Queue {
+    R val[QMAX][6];                    // um2, um1, u0, up1, up2, uor
+    R res[QMAX];
+    unsigned short slot[NSLOT][NT];    // queue entry of (slot, thread)
+    int count;
+
+    __device__ __forceinline__ void reset()
+    {
+        if (threadIdx.x == 0) count = 0;
+    }
+    // value of the reconstruction in slot k of this thread (placeholder if queued)
+    __device__ __forceinline__ R defer(R um2, R um1, R u0, R up1, R up2, int k, unsigned &mask)
+    {
+        R uor;
+        if (mp5_smooth(um2, um1, u0, up1, up2, uor)) return uor;
+        int e = atomicAdd(&count, 1);
+        if (e < QMAX) {
+            val[e][0] = um2;
+            val[e][1] = um1;
+            val[e][2] = u0;
+            val[e][3] = up1;
+            val[e][4] = up2;
+            val[e][5] = uor;
+            slot[k][threadIdx.x] = (unsigned short)e;
+            mask |= 1u << k;
+            return uor;
+        }
+        return mp5_limit(um2, um1, u0, up1, up2, uor);
+    }
+    // whole block, between two barriers
+    __device__ __forceinline__ void process()
+    {
+        const int m = count < QMAX ? count : QMAX;
+        for (int e = threadIdx.x; e < m; e += NT)
+            res[e] = mp5_limit(val[e][0], val[e][1], val[e][2], val[e][3], val[e][4], val[e][5]);
+    }
+    __device__ __forceinline__ R get(int k) const { return res[slot[k][threadIdx.x]]; }
+};
 
 // left state at i+1/2 from s[0..5] = u_{i-2..i+3}, and the mirrored right state
 template <typename R>
@@ -318,15 +382,52 @@ __device__ __forceinline__ bool c2p_ok(const C2PInv &q, double W)
     return c2p_eval(q, W, v2, r);
 }
 
+// FP32 Newton iterations on the same f(W), used by the mixed path to refine the
+// starting guess before the FP64 iteration (FP32 issues 64x faster than FP64 on
+// GB300).  Stops once a step is below 4e-6 W (FP32 cannot resolve much further);
+// returns the refined guess, or W0 unchanged if an iterate leaves the domain or
+// is not finite.  The FP64 iteration that follows decides the result.
+__device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &iters)
+{
+    const float D = (float)q.D, S2 = (float)q.S2, B2 = (float)q.B2, SB = (float)q.SB;
+    const float U = (float)q.U, gm1g = (float)q.gm1g, SB2 = SB * SB;
+    float W = (float)W0;
+    iters = 0;
+    if (!(W > 0.f) || !isfinite(W)) return W0;
+    for (int k = 0; k < 8; k++) {
+        float wb = W + B2;
+        float r = 1.f / (W * wb);
+        float iW = wb * r, iwb = W * r;
+        float v2 = (S2 * W * W + SB2 * (B2 + 2.f * W)) * (r * r);
+        if (!(v2 < 1.f) || !isfinite(v2)) return W0;
+        float omv2 = 1.f - v2;
+        float isq = rsqrtf(omv2);
+        float sq1 = omv2 * isq;
+        float iW2 = iW * iW;
+        float p = gm1g * (W * omv2 - D * sq1);
+        float dv2 = -2.f * SB2 * (iW2 * iW) * iwb - 2.f * v2 * iwb;
+        float dp = gm1g * (omv2 - W * dv2 + 0.5f * D * dv2 * isq);
+        float f = W - p + 0.5f * (1.f + v2) * B2 - 0.5f * SB2 * iW2 - U;
+        float df = 1.f - dp + 0.5f * B2 * dv2 + SB2 * (iW2 * iW);
+        float dW = -f / df;
+        float Wn = W + dW;
+        iters++;
+        if (!(Wn > 0.f) || !isfinite(Wn)) return W0;
+        W = Wn;
+        if (fabsf(dW) <= 4e-6f * W) break;
+    }
+    return (double)W;
+}
+
 // Newton on f(W) = W - p(W) + (1 + v^2) B^2/2 - (S.B)^2/(2 W^2) - U with the
 // analytic derivative; a trial point outside the domain halves the step; stop
-// when |dW| <= tol W, after one more polishing step.  The domain check of a trial
+// after an undamped step with |dW| <= tol W and one more polishing step.  The domain check of a trial
 // point computes v^2 and 1/(W (W+B^2)) there, and the next iteration reuses both,
 // so an iteration costs two divisions and one reciprocal square root.
 // Returns true on success.  prim = (rho, vx, vy, vz, p); B the cell-centred field.
 __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, double gam,
                                            double W0, double tol, int maxit, double *prim,
-                                           double &Wout, int &iters)
+                                           double &Wout, int &iters, int pre32, int &iters32)
 {
     C2PInv q;
     q.D = u[0];
@@ -336,6 +437,8 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     q.U = u[4];
     q.gm1g = (gam - 1.0) / gam;
     const double SB2 = q.SB * q.SB;
+    iters32 = 0;
+    if (pre32) W0 = c2p_pre32(q, W0, iters32);
     double W = W0, v2 = 0.0, r = 0.0;
     bool ok = c2p_eval(q, W, v2, r);
     for (int k = 0; k < 64 && !ok; k++) {
@@ -378,7 +481,7 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
             conv = true;
             break;
         }
-        if (le(step, tol * W)) polish = true;
+        if (lam == 1.0 && le(step, tol * W)) polish = true;
     }
     iters = it;
     Wout = W;
@@ -403,6 +506,25 @@ __device__ __forceinline__ double warp_max(double v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+__device__ __forceinline__ float warp_max_r(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// maximum of non-negative doubles through their ordered integer keys (integer pipe)
+__device__ __forceinline__ double warp_max_r(double v)
+{
+    long long k = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        long long q = __shfl_xor_sync(0xffffffffu, k, o);
+        k = q > k ? q : k;
+    }
+    return __longlong_as_double(k);
 }
 
 __device__ __forceinline__ double warp_sum(double v)

@@ -32,6 +32,7 @@ struct echo_ctx {
 
     // conserved state (double): U[5n], U0[5n], Bf[3n], Bf0[3n]; warm guess W[n]
     double *U, *U0, *Bf, *Bf0, *W;
+    float *Bf32;    // mixed path: float copy of the face field read by the sweeps
     // work buffers in the reconstruction precision R (double or float)
     void *prim;     // [8][n]  rho, vx, vy, vz, p, Bx, By, Bz at centres
     void *flux;     // [5][n]  HLL flux of one direction
@@ -42,8 +43,8 @@ struct echo_ctx {
     double *partials;       // reduction scratch of the diagnostics
     double *dres;           // reduction results (device)
     double *stage8;         // staging for host outputs [8][n] (allocated on demand)
-    float *mlp_w;           // learned-guess weights (device), or NULL
-    float *guess;           // learned guesses [n] (allocated on demand)
+    void *mlp_w;            // learned-guess weights in their device form, or NULL
+    float *guess;           // learned guesses [n] (allocated with the weights)
 
     bool has_state;
     long launches;
@@ -87,8 +88,9 @@ constexpr int DIAG_Q = 24;  // quantities per block partial
 // Per-precision kernel launchers (one translation unit per precision).
 template <typename R>
 struct Path {
-    // INT + C2P into the work prims (R).  stage: 1..3 (0 for a one-off call);
-    // update_w: store the converged W as the next warm guess.
+    // (learned guesses when selected and loaded, then) INT + C2P into the work prims
+    // (R).  stage: 1..3 (0 for a one-off call); update_w: store the converged W as
+    // the next warm guess.
     static void int_c2p(echo_ctx *c, int stage, long step, int update_w);
     // sweeps + DER (steps 2-3), want_amax on the first stage of a step
     static void sweeps(echo_ctx *c, int want_amax);
@@ -112,11 +114,12 @@ void launch_diag_mode(echo_ctx *c, int mode, const double *a, const double *b);
 void launch_copy_state(echo_ctx *c, double *dst_u, double *dst_b, const double *src_u,
                        const double *src_b);
 void launch_w_from_cold(echo_ctx *c);
+// refresh the float copy of the face field (mixed path) after the state changed
+void launch_bf32(echo_ctx *c);
 double probe_fma_peak(echo_ctx *c, int fp64);
 // error text of calls without a context (returned by echo_last_error(NULL))
 void set_global_error(const char *msg);
-// learned guess: W0 for every cell into c->guess; harvest of training states
-void launch_mlp_guess(echo_ctx *c);
+// harvest of training states (features, converged W/U)
 void launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,
                         long capacity, unsigned long long *count);
 

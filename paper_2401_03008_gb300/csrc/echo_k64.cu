@@ -72,7 +72,7 @@ void launch_curl_apot(echo_ctx *c, const double *apot)
 // primitives in double for output: INT + C2P with the warm guess, W left untouched
 void launch_prims_out(echo_ctx *c, double *out8)
 {
-    C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, ECHO_GUESS_PREV};
+    C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, ECHO_GUESS_PREV, 0};
     launch(c, K_C2P, k_int_c2p<double>, nblocks(c->g.n, BS), BS, 0, c->g, (const double *)c->U,
            (const double *)c->Bf, c->W, (const float *)nullptr, out8, par, c->sc, 0, -1L, 0, 0);
 }
@@ -91,6 +91,19 @@ void launch_copy_state(echo_ctx *c, double *dst_u, double *dst_b, const double *
 {
     launch(c, K_MISC, k_copy2, nblocks(5 * c->g.n, BS), BS, 0, 5 * c->g.n, 3 * c->g.n, dst_u,
            dst_b, src_u, src_b);
+}
+
+__global__ void __launch_bounds__(BS) k_to_float(long m, const double *__restrict__ in, float *__restrict__ out)
+{
+    long q = blockIdx.x * (long)BS + threadIdx.x;
+    if (q < m) out[q] = (float)in[q];
+}
+
+void launch_bf32(echo_ctx *c)
+{
+    if (!c->Bf32) return;
+    long m = 3 * c->g.n;
+    launch(c, K_MISC, k_to_float, nblocks(m, BS), BS, 0, m, (const double *)c->Bf, c->Bf32);
 }
 
 // cold guess W0 = U for a resumed state without a stored guess

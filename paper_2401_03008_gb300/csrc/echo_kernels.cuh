@@ -12,6 +12,7 @@
 #pragma once
 
 #include "echo_internal.h"
+#include "echo_mlp.cuh"
 
 namespace echo {
 
@@ -23,6 +24,9 @@ __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
 // ---------------------------------------------------------------------------
 // step 1: INT + C2P
 // ---------------------------------------------------------------------------
+// guess: the learned starting guesses W0 (one float per cell, from k_mlp_guess) when
+// that guess is selected, else NULL.  An unusable guess falls back to the previous
+// W and is counted.
 template <typename R>
 __global__ void __launch_bounds__(BS)
 k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
@@ -34,7 +38,7 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
     if (count && __reduce_or_sync(0xffffffffu, (unsigned)sc->halt)) return;
     const long n = g.n;
     long c = blockIdx.x * (long)BS + threadIdx.x;
-    unsigned it = 0;
+    unsigned it = 0, it32 = 0;
     bool active = c < n, bad = false, fb = false;
     if (active) {
         int i, j, k;
@@ -51,9 +55,7 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
 #pragma unroll
         for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
         double W0;
-        if (par.guess == 1) {
-            W0 = u[4];
-        } else if (par.guess == 2 && guess) {
+        if (guess) {
             W0 = (double)guess[c];
             C2PInv q;
             q.D = u[0];
@@ -65,13 +67,16 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
                 W0 = W[c];
                 fb = true;
             }
+        } else if (par.guess == 1) {
+            W0 = u[4];
         } else {
             W0 = W[c];
         }
         double p[5], Wn;
-        int iters;
-        bad = !c2p_newton(u, B, g.gam, W0, par.tol, par.maxit, p, Wn, iters);
+        int iters, iters32;
+        bad = !c2p_newton(u, B, g.gam, W0, par.tol, par.maxit, p, Wn, iters, par.pre32, iters32);
         it = (unsigned)iters;
+        it32 = (unsigned)iters32;
 #pragma unroll
         for (int v = 0; v < 5; v++) prim[v * n + c] = (R)p[v];
 #pragma unroll
@@ -80,12 +85,14 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
     }
     if (!count) return;
     unsigned s = __reduce_add_sync(0xffffffffu, it);
+    unsigned s32 = __reduce_add_sync(0xffffffffu, it32);
     unsigned m = __reduce_max_sync(0xffffffffu, it);
     unsigned na = __popc(__ballot_sync(0xffffffffu, active));
     unsigned nb = __popc(__ballot_sync(0xffffffffu, bad));
     unsigned nf = __popc(__ballot_sync(0xffffffffu, fb));
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&sc->it_sum, (unsigned long long)s);
+        if (s32) atomicAdd(&sc->it32_sum, (unsigned long long)s32);
         atomicAdd(&sc->c2p_calls, (unsigned long long)na);
         atomicMax(&sc->it_max, m);
         if (nf) atomicAdd(&sc->fallbacks, nf);
@@ -97,34 +104,92 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
     }
 }
 
+// Learned Newton starting guesses W0 = U y for every cell.  Persistent blocks: the
+// weights go to shared memory once per block, which then walks the grid in steps
+// of the whole launch.  BT: precision of the face field read for the features
+// (the float mirror on the mixed path).
+constexpr int MLP_BS = 128;
+
+template <typename BT>
+__global__ void __launch_bounds__(MLP_BS)
+k_mlp_guess(Grid g, const double *__restrict__ U, const BT *__restrict__ Bf,
+            const MlpDev *__restrict__ w, float *__restrict__ guess)
+{
+    __shared__ __align__(16) MlpDev sw;
+    load_mlp_shared(sw, w);
+    const int lane = threadIdx.x & 31;
+    const long n = g.n;
+    for (long base = blockIdx.x * (long)MLP_BS; base < n; base += (long)gridDim.x * MLP_BS) {
+        const long c = base + threadIdx.x;
+        double u[5] = {1.0, 0.0, 0.0, 0.0, 2.0}, B[3] = {0.0, 0.0, 0.0};
+        if (c < n) {
+            int i, j, k;
+            coords(g, c, i, j, k);
+            for (int d = 0; d < 3; d++) {
+                const BT *b = Bf + d * n;
+                B[d] = (double)int_c(__ldg(b + shifted_rt(g, i, j, k, d, -2)),
+                                     __ldg(b + shifted_rt(g, i, j, k, d, -1)), __ldg(b + c),
+                                     __ldg(b + shifted_rt(g, i, j, k, d, 1)), g.ho);
+            }
+            for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
+        }
+        float x[NIN];
+        mlp_features(u, B, x);
+        const float y = mlp_warp_forward(sw, x, lane);
+        if (c < n) guess[c] = (float)(u[4] * (double)y);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // steps 2: reconstruction + HLL at the faces along D
 // ---------------------------------------------------------------------------
+// queue capacity of the deferred MP5 limiting: two entries per thread on average
+constexpr int QMAX = 2 * BS;
+
 template <typename R, int D>
 __global__ void __launch_bounds__(BS)
-k_flux(Grid g, const R *__restrict__ prim, const double *__restrict__ Bf, R *__restrict__ flux,
+k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restrict__ flux,
        R *__restrict__ fd, DevScalars *sc, int want_amax)
 {
     if (sc->halt) return;
+    __shared__ Mp5Queue<R, 14, QMAX, BS> q;
+    q.reset();
+    __syncthreads();
     const long n = g.n;
     long f = blockIdx.x * (long)BS + threadIdx.x;
-    double amax = 0.0;
-    if (f < n) {
+    const bool active = f < n;
+    R amax = R(0);
+    long cs[6];
+    R L[8], Rt[8];
+    unsigned mask = 0;
+    if (active) {
         int i, j, k;
         coords(g, f, i, j, k);
-        long cs[6];
 #pragma unroll
         for (int m = 0; m < 6; m++) cs[m] = shifted<D>(g, i, j, k, m - 2);
-        R L[8], Rt[8];
 #pragma unroll
         for (int v = 0; v < 8; v++) {
             if (v == 5 + D) continue;
+            const int vi = v < 5 + D ? v : v - 1;  // 0..6 over the reconstructed variables
             R s[6];
 #pragma unroll
             for (int m = 0; m < 6; m++) s[m] = ld(prim + v * n + cs[m]);
-            mp5_lr(s, L[v], Rt[v]);
+            L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], 2 * vi, mask);
+            Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], 2 * vi + 1, mask);
         }
-        const R bn = (R)Bf[D * n + f];
+    }
+    __syncthreads();
+    q.process();
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+            if (v == 5 + D) continue;
+            const int vi = v < 5 + D ? v : v - 1;
+            if (mask & (1u << (2 * vi))) L[v] = q.get(2 * vi);
+            if (mask & (1u << (2 * vi + 1))) Rt[v] = q.get(2 * vi + 1);
+        }
+        const R bn = Bf[D * n + f];
         L[5 + D] = bn;
         Rt[5 + D] = bn;
         // positivity: reset a state to the first-order (cell) value
@@ -157,11 +222,11 @@ k_flux(Grid g, const R *__restrict__ prim, const double *__restrict__ Bf, R *__r
         if (gtz(s)) {
             R is = R(1) / s;
 #pragma unroll
-            for (int q = 0; q < 5; q++)
-                flux[q * n + f] = (ap * FL[q] + am * FR[q] - ap * am * (UR[q] - UL[q])) * is;
+            for (int qq = 0; qq < 5; qq++)
+                flux[qq * n + f] = (ap * FL[qq] + am * FR[qq] - ap * am * (UR[qq] - UL[qq])) * is;
         } else {
 #pragma unroll
-            for (int q = 0; q < 5; q++) flux[q * n + f] = R(0.5) * (FL[q] + FR[q]);
+            for (int qq = 0; qq < 5; qq++) flux[qq * n + f] = R(0.5) * (FL[qq] + FR[qq]);
         }
         constexpr int E1 = (D + 1) % 3;
         fd[f] = L[1 + D];
@@ -170,18 +235,20 @@ k_flux(Grid g, const R *__restrict__ prim, const double *__restrict__ Bf, R *__r
         fd[3 * n + f] = Rt[1 + E1];
         fd[4 * n + f] = ap;
         fd[5 * n + f] = am;
-        amax = (double)rmax(ap, am);
+        amax = rmax(ap, am);
     }
     if (want_amax) {
-        __shared__ double red[BS / 32];
-        double m = warp_max(amax);
+        // block maximum in R (non-negative values), one conversion per block
+        __shared__ R red[BS / 32];
+        R m = warp_max_r(amax);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
         __syncthreads();
         if (threadIdx.x < 32) {
-            double v = threadIdx.x < BS / 32 ? red[threadIdx.x] : 0.0;
-            v = warp_max(v);
-            if (threadIdx.x == 0 && v > 0.0)
-                atomicMax(&sc->amax_bits, (unsigned long long)__double_as_longlong(v));
+            R v = threadIdx.x < BS / 32 ? red[threadIdx.x] : R(0);
+            v = warp_max_r(v);
+            const double vd = (double)v;
+            if (threadIdx.x == 0 && vd > 0.0)
+                atomicMax(&sc->amax_bits, (unsigned long long)__double_as_longlong(vd));
         }
     }
 }
@@ -218,38 +285,60 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
 // ---------------------------------------------------------------------------
 template <typename R, int C>
 __global__ void __launch_bounds__(BS)
-k_uct(Grid g, const double *__restrict__ Bf, const R *__restrict__ fda, const R *__restrict__ fdb,
+k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__restrict__ fdb,
       R *__restrict__ E, DevScalars *sc)
 {
     if (sc->halt) return;
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    __shared__ Mp5Queue<R, 12, QMAX, BS> q;
+    q.reset();
+    __syncthreads();
     const long n = g.n;
     long e = blockIdx.x * (long)BS + threadIdx.x;
-    if (e >= n) return;
-    int i, j, k;
-    coords(g, e, i, j, k);
+    const bool active = e < n;
+    // slots: va[s][t] = 4 s + t, vb[s][t] = 4 s + 2 + t, Ba[t] = 8 + t, Bb[s] = 10 + s
+    R r[12];
+    unsigned mask = 0;
     long sb[6], sa[6];
+    if (active) {
+        int i, j, k;
+        coords(g, e, i, j, k);
 #pragma unroll
-    for (int m = 0; m < 6; m++) {
-        sb[m] = shifted<B>(g, i, j, k, m - 2);
-        sa[m] = shifted<A>(g, i, j, k, m - 2);
+        for (int m = 0; m < 6; m++) {
+            sb[m] = shifted<B>(g, i, j, k, m - 2);
+            sa[m] = shifted<A>(g, i, j, k, m - 2);
+        }
+        R s[6];
+#pragma unroll
+        for (int qs = 0; qs < 2; qs++) {
+#pragma unroll
+            for (int m = 0; m < 6; m++) s[m] = ld(fda + (2 * qs) * n + sb[m]);
+            r[4 * qs + 0] = q.defer(s[0], s[1], s[2], s[3], s[4], 4 * qs + 0, mask);
+            r[4 * qs + 1] = q.defer(s[5], s[4], s[3], s[2], s[1], 4 * qs + 1, mask);
+#pragma unroll
+            for (int m = 0; m < 6; m++) s[m] = ld(fda + (2 * qs + 1) * n + sb[m]);
+            r[4 * qs + 2] = q.defer(s[0], s[1], s[2], s[3], s[4], 4 * qs + 2, mask);
+            r[4 * qs + 3] = q.defer(s[5], s[4], s[3], s[2], s[1], 4 * qs + 3, mask);
+        }
+#pragma unroll
+        for (int m = 0; m < 6; m++) s[m] = ld(Bf + A * n + sb[m]);
+        r[8] = q.defer(s[0], s[1], s[2], s[3], s[4], 8, mask);
+        r[9] = q.defer(s[5], s[4], s[3], s[2], s[1], 9, mask);
+#pragma unroll
+        for (int m = 0; m < 6; m++) s[m] = ld(Bf + B * n + sa[m]);
+        r[10] = q.defer(s[0], s[1], s[2], s[3], s[4], 10, mask);
+        r[11] = q.defer(s[5], s[4], s[3], s[2], s[1], 11, mask);
     }
-    R va[2][2], vb[2][2], Ba[2], Bb[2], s[6];
+    __syncthreads();
+    q.process();
+    __syncthreads();
+    if (!active) return;
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-#pragma unroll
-        for (int m = 0; m < 6; m++) s[m] = ld(fda + (2 * q) * n + sb[m]);
-        mp5_lr(s, va[q][0], va[q][1]);
-#pragma unroll
-        for (int m = 0; m < 6; m++) s[m] = ld(fda + (2 * q + 1) * n + sb[m]);
-        mp5_lr(s, vb[q][0], vb[q][1]);
-    }
-#pragma unroll
-    for (int m = 0; m < 6; m++) s[m] = (R)Bf[A * n + sb[m]];
-    mp5_lr(s, Ba[0], Ba[1]);
-#pragma unroll
-    for (int m = 0; m < 6; m++) s[m] = (R)Bf[B * n + sa[m]];
-    mp5_lr(s, Bb[0], Bb[1]);
+    for (int k2 = 0; k2 < 12; k2++)
+        if (mask & (1u << k2)) r[k2] = q.get(k2);
+    R va[2][2] = {{r[0], r[1]}, {r[4], r[5]}};
+    R vb[2][2] = {{r[2], r[3]}, {r[6], r[7]}};
+    R Ba[2] = {r[8], r[9]}, Bb[2] = {r[10], r[11]};
     R apa = rmax(ld(fda + 4 * n + e), ld(fda + 4 * n + sb[3]));
     R ama = rmax(ld(fda + 5 * n + e), ld(fda + 5 * n + sb[3]));
     R apb = rmax(ld(fdb + 4 * n + e), ld(fdb + 4 * n + sa[3]));
@@ -280,7 +369,7 @@ template <typename R>
 __global__ void __launch_bounds__(BS)
 k_rk(Grid g, int stage, const R *__restrict__ E, const R *__restrict__ rhs,
      double *__restrict__ U, double *__restrict__ U0, double *__restrict__ Bf,
-     double *__restrict__ Bf0, DevScalars *sc)
+     double *__restrict__ Bf0, float *__restrict__ Bf32, DevScalars *sc)
 {
     if (sc->halt) return;
     const long n = g.n;
@@ -302,14 +391,17 @@ k_rk(Grid g, int stage, const R *__restrict__ E, const R *__restrict__ rhs,
                 pu0 = Bf0 + (v - 5) * n + c;
             }
             u = *pu;
+            double un;
             if (stage == 1) {
                 *pu0 = u;
-                *pu = u + dt * r;
+                un = u + dt * r;
             } else if (stage == 2) {
-                *pu = 0.75 * (*pu0) + 0.25 * (u + dt * r);
+                un = 0.75 * (*pu0) + 0.25 * (u + dt * r);
             } else {
-                *pu = (*pu0) * (1.0 / 3.0) + 2.0 / 3.0 * (u + dt * r);
+                un = (*pu0) * (1.0 / 3.0) + 2.0 / 3.0 * (u + dt * r);
             }
+            *pu = un;
+            if (v >= 5 && Bf32) Bf32[(v - 5) * n + c] = (float)un;
         }
     }
     if (stage == 3 && blockIdx.x == 0 && threadIdx.x == 0) sc->step += 1;
@@ -342,14 +434,32 @@ __global__ void __launch_bounds__(BS) k_to_double(long m, const R *__restrict__ 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// the face field in R: the double state itself, or its float mirror
+template <typename R> inline const R *face_field(echo_ctx *c);
+template <> inline const double *face_field<double>(echo_ctx *c) { return c->Bf; }
+template <> inline const float *face_field<float>(echo_ctx *c) { return c->Bf32; }
+
 template <typename R>
 void Path<R>::int_c2p(echo_ctx *c, int stage, long step, int update_w)
 {
-    C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, c->cfg.c2p_guess};
-    if (par.guess == ECHO_GUESS_MLP && !c->guess) par.guess = ECHO_GUESS_PREV;
+    // the mixed path refines the guess with FP32 Newton iterations first
+    C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, c->cfg.c2p_guess, c->mixed ? 1 : 0};
+    const bool mlp = par.guess == ECHO_GUESS_MLP && c->mlp_w && c->guess;
+    if (par.guess == ECHO_GUESS_MLP && !mlp) par.guess = ECHO_GUESS_PREV;
+    if (mlp) {
+        // persistent grid: as many blocks as can be resident at once
+        int nsm = 152, per_sm = 1;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->cfg.device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_guess<R>, MLP_BS, 0);
+        unsigned nb = nblocks(c->g.n, MLP_BS);
+        const unsigned cap = (unsigned)(nsm * (per_sm > 0 ? per_sm : 1));
+        if (nb > cap) nb = cap;
+        launch(c, K_MLP, k_mlp_guess<R>, nb, MLP_BS, 0, c->g, (const double *)c->U,
+               face_field<R>(c), (const MlpDev *)c->mlp_w, c->guess);
+    }
     launch(c, K_C2P, k_int_c2p<R>, nblocks(c->g.n, BS), BS, 0, c->g, (const double *)c->U,
-           (const double *)c->Bf, c->W, (const float *)c->guess, (R *)c->prim, par, c->sc,
-           stage, step, update_w, 1);
+           (const double *)c->Bf, c->W, mlp ? (const float *)c->guess : (const float *)nullptr,
+           (R *)c->prim, par, c->sc, stage, step, update_w, 1);
 }
 
 template <typename R>
@@ -357,14 +467,15 @@ void Path<R>::sweeps(echo_ctx *c, int want_amax)
 {
     const unsigned nb = nblocks(c->g.n, BS);
     const R *prim = (const R *)c->prim;
+    const R *bf = face_field<R>(c);
     R *flux = (R *)c->flux, *rhs = (R *)c->rhs;
-    launch(c, K_FLUX_X, k_flux<R, 0>, nb, BS, 0, c->g, prim, (const double *)c->Bf, flux,
+    launch(c, K_FLUX_X, k_flux<R, 0>, nb, BS, 0, c->g, prim, bf, flux,
            (R *)c->fdat[0], c->sc, want_amax);
     launch(c, K_DER_X, k_der<R, 0>, nb, BS, 0, c->g, (const R *)flux, rhs, 1, c->sc);
-    launch(c, K_FLUX_Y, k_flux<R, 1>, nb, BS, 0, c->g, prim, (const double *)c->Bf, flux,
+    launch(c, K_FLUX_Y, k_flux<R, 1>, nb, BS, 0, c->g, prim, bf, flux,
            (R *)c->fdat[1], c->sc, want_amax);
     launch(c, K_DER_Y, k_der<R, 1>, nb, BS, 0, c->g, (const R *)flux, rhs, 0, c->sc);
-    launch(c, K_FLUX_Z, k_flux<R, 2>, nb, BS, 0, c->g, prim, (const double *)c->Bf, flux,
+    launch(c, K_FLUX_Z, k_flux<R, 2>, nb, BS, 0, c->g, prim, bf, flux,
            (R *)c->fdat[2], c->sc, want_amax);
     launch(c, K_DER_Z, k_der<R, 2>, nb, BS, 0, c->g, (const R *)flux, rhs, 0, c->sc);
 }
@@ -374,17 +485,18 @@ void Path<R>::uct(echo_ctx *c)
 {
     const unsigned nb = nblocks(c->g.n, BS);
     const R *f0 = (const R *)c->fdat[0], *f1 = (const R *)c->fdat[1], *f2 = (const R *)c->fdat[2];
+    const R *bf = face_field<R>(c);
     // E_z from x-faces (a) and y-faces (b); E_x from y and z; E_y from z and x
-    launch(c, K_UCT_Z, k_uct<R, 2>, nb, BS, 0, c->g, (const double *)c->Bf, f0, f1, (R *)c->E, c->sc);
-    launch(c, K_UCT_X, k_uct<R, 0>, nb, BS, 0, c->g, (const double *)c->Bf, f1, f2, (R *)c->E, c->sc);
-    launch(c, K_UCT_Y, k_uct<R, 1>, nb, BS, 0, c->g, (const double *)c->Bf, f2, f0, (R *)c->E, c->sc);
+    launch(c, K_UCT_Z, k_uct<R, 2>, nb, BS, 0, c->g, bf, f0, f1, (R *)c->E, c->sc);
+    launch(c, K_UCT_X, k_uct<R, 0>, nb, BS, 0, c->g, bf, f1, f2, (R *)c->E, c->sc);
+    launch(c, K_UCT_Y, k_uct<R, 1>, nb, BS, 0, c->g, bf, f2, f0, (R *)c->E, c->sc);
 }
 
 template <typename R>
 void Path<R>::rk(echo_ctx *c, int stage)
 {
     launch(c, K_RK, k_rk<R>, nblocks(c->g.n, BS), BS, 0, c->g, stage, (const R *)c->E,
-           (const R *)c->rhs, c->U, c->U0, c->Bf, c->Bf0, c->sc);
+           (const R *)c->rhs, c->U, c->U0, c->Bf, c->Bf0, c->Bf32, c->sc);
 }
 
 template <typename R>

@@ -61,7 +61,7 @@ class Diag(C.Structure):
                 ("tot", C.c_double * 8), ("newton_it_mean", C.c_double),
                 ("newton_it_max", C.c_int), ("c2p_calls", C.c_long),
                 ("c2p_fallbacks", C.c_long), ("c2p_failures", C.c_long),
-                ("nonfinite", C.c_long), ("step", C.c_long)]
+                ("nonfinite", C.c_long), ("step", C.c_long), ("newton_it32_mean", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -142,7 +142,7 @@ class Solver:
     """One libecho context: a periodic grid with its state on the GPU."""
 
     def __init__(self, nx, ny, nz, L=(1.0, 1.0, 1.0), gamma=4.0 / 3.0, cfl=0.4, ho=1,
-                 precision="fp64", guess="prev", tol=1e-12, maxit=100, device=0,
+                 precision="fp64", guess="prev", tol=1e-6, maxit=100, device=0,
                  stream=None):
         self.L = lib()
         cfg = Config()

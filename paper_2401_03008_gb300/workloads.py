@@ -318,3 +318,26 @@ class Turbulence:
             coef = self.aB / self._kn * self.eB[:, c]
             out[c] = _synth(n, self.modes, coef, self.phB - 0.5 * np.pi, offs[c])
         return out
+
+
+# ---------------------------------------------------------------------------
+# Initial parameters of the learned Newton guess (random inputs of training)
+# ---------------------------------------------------------------------------
+
+MLP_SHAPES = [(64, 5), (64,), (64, 64), (64,), (64,), (1,)]  # W1, b1, W2, b2, w3, b3
+
+
+def mlp_init(seed):
+    """Glorot-uniform weights and zero biases, flattened in the order W1, b1, W2, b2,
+    w3, b3 (4609 float32 values); seeded PCG64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for shape in MLP_SHAPES:
+        if len(shape) == 2 or shape == (64,) and len(parts) == 4:
+            fan_in = shape[1] if len(shape) == 2 else 64
+            fan_out = shape[0] if len(shape) == 2 else 1
+            lim = math.sqrt(6.0 / (fan_in + fan_out))
+            parts.append(rng.uniform(-lim, lim, shape).ravel())
+        else:
+            parts.append(np.zeros(int(np.prod(shape))))
+    return np.concatenate(parts).astype(np.float32)

@@ -13,7 +13,7 @@ from oracle import oracle as orc
 
 
 class BruteRHS:
-    def __init__(self, cons, bf, W, L=(1.0, 1.0, 1.0), gam=4.0 / 3.0, ho=1, tol=1e-12):
+    def __init__(self, cons, bf, W, L=(1.0, 1.0, 1.0), gam=4.0 / 3.0, ho=1, tol=1e-6):
         self.cons, self.bf, self.W = cons, bf, W
         self.nz, self.ny, self.nx = cons.shape[1:]
         self.N = (self.nx, self.ny, self.nz)

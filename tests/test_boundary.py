@@ -35,7 +35,7 @@ def test_config_default():
     cfg = echo.Config()
     assert echo.lib().echo_config_default(C.byref(cfg)) == echo.ECHO_OK
     assert (cfg.nx, cfg.uct, cfg.ho, cfg.precision) == (32, 1, 1, echo.FP64)
-    assert cfg.gamma_ad == pytest.approx(4 / 3) and cfg.cfl == 0.4 and cfg.c2p_tol == 1e-12
+    assert cfg.gamma_ad == pytest.approx(4 / 3) and cfg.cfl == 0.4 and cfg.c2p_tol == 1e-6
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("lz", -1.0), ("gamma_ad", 1.0),

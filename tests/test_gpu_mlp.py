@@ -25,11 +25,16 @@ def _samples(n, seed):
 def test_forward_matches_oracle():
     import torch
     x, t = _samples(1000, 61)  # not a multiple of 32: ragged last warp
-    w = mlp.init(62)
+    w = wl.mlp_init(62)
     y = echo.mlp_forward(w, torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
-    # the oracle gets the features the GPU saw (float32) and rounds at the same points
+    # the oracle gets the features the GPU saw (float32) and rounds at the same points.
+    # Inference uses the hardware tanh (absolute error about 2^-11 per activation):
+    # through the 64 x 64 layer and the output dot product that stays below
+    # sum |w3| * 2^-10 plus a bf16 rounding flip or two of the hidden layer
     ref, _ = mlp.forward(w.astype(np.float64), x.astype(np.float32).astype(np.float64), bf=True)
-    assert np.max(np.abs(y - ref)) < 1e-3
+    p = mlp.unpack(w.astype(np.float64))
+    bound = np.sum(np.abs(p["w3"])) * 2.0 ** -10 + 2e-3
+    assert np.max(np.abs(y - ref)) < bound
     ref64, _ = mlp.forward(w.astype(np.float64), x)
     assert np.max(np.abs(y - ref64)) < 2e-2
 
@@ -37,7 +42,7 @@ def test_forward_matches_oracle():
 def test_gradient_matches_oracle():
     import torch
     x, t = _samples(512, 63)
-    w = mlp.init(64)
+    w = wl.mlp_init(64)
     xf = x.astype(np.float32)
     loss, g = echo.mlp_grad(w, torch.from_numpy(xf).cuda(),
                             torch.from_numpy(t.astype(np.float32)).cuda())
@@ -71,7 +76,7 @@ def test_trained_guess_gains_over_cold_guess():
     target = torch.empty(cap, dtype=torch.float32, device="cuda")
     cnt = s.mlp_harvest(10, 8, feats, target)
     assert cnt == min(cap, 10 * 3 * n ** 3 // 8)
-    w0 = mlp.init(102)
+    w0 = wl.mlp_init(102)
     w, hist = echo.mlp_train(feats[:cnt].contiguous(), target[:cnt].contiguous(), w0, epochs=6,
                              batch=1024, lr=3e-3, lr_decay=0.7)
     assert hist[-1] < 0.05 * hist[0], hist

@@ -189,12 +189,15 @@ def test_c2p_failure_rolls_back():
     the state, t and step count are those at the start of the failed step."""
     n = (16, 16, 16)
     c, st = cpa_state(n, (1, 1, 1))
-    s = echo.Solver(*n, maxit=3)
+    # stage 1 starts from the exact W of the initial data and converges in 2
+    # iterations; the later stages need 3, so a cap of 2 fails there
+    s = echo.Solver(*n, maxit=2)
     s.set_state(*st)
     cons0, bf0, _, t0, step0 = s.get_state()
     with pytest.raises(echo.EchoError) as ei:
         s.step(3)
     assert ei.value.status == echo.ECHO_ERR_C2P
+    assert "stage 2" in str(ei.value) or "stage 3" in str(ei.value), str(ei.value)
     cons1, bf1, _, t1, step1 = s.get_state()
     assert np.array_equal(cons0, cons1) and np.array_equal(bf0, bf1)
     assert t1 == t0 and step1 == step0

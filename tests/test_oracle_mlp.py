@@ -20,7 +20,7 @@ def test_gradient_matches_finite_differences():
     u, B, W = _batch(40, 51)
     x = mlp.features(u, B)
     t = W / u[4]
-    theta = mlp.init(52).astype(np.float64)
+    theta = wl.mlp_init(52).astype(np.float64)
     loss, g = mlp.loss_grad(theta, x, t)
     rng = np.random.default_rng(53)
     for i in rng.choice(mlp.NPARAM, 60, replace=False).tolist() + [mlp.NPARAM - 1, 0]:
@@ -62,7 +62,7 @@ def test_bf16_emulation_is_close_to_fp64():
     u, B, W = _batch(256, 56)
     x = mlp.features(u, B)
     t = W / u[4]
-    theta = mlp.init(57).astype(np.float64)
+    theta = wl.mlp_init(57).astype(np.float64)
     l64, g64 = mlp.loss_grad(theta, x, t)
     lbf, gbf = mlp.loss_grad(theta, x, t, bf=True)
     assert abs(lbf - l64) / l64 < 1e-2

@@ -387,3 +387,19 @@ def test_uct_reduces_to_hll_along_b():
         FR = vbR * BaR - vaR * Bb
         F = (apb * FL + amb * FR - apb * amb * (BaR - BaL)) / (apb + amb)
         assert E == pytest.approx(F, abs=1e-14)
+
+
+def test_c2p_stopping_rule_reaches_rounding_floor():
+    """An undamped step below tol W followed by the polishing step leaves the root
+    at the FP64 rounding floor: the default tolerance gives the same W as a far
+    tighter one, from cold starts on random states."""
+    prim, B = wl.random_states(2000, seed=17)
+    u = _cons_of(prim, B)
+    _, W6, it6, f6 = orc.c2p_batch(u, B, u[4].copy(), GAM)
+    _, W12, it12, f12 = orc.c2p_batch(u, B, u[4].copy(), GAM, tol=1e-12)
+    assert f6 == 0 and f12 == 0
+    # the rounding floor of W is about eps U / f' (f is a sum of terms of size U)
+    eps = np.finfo(np.float64).eps
+    assert np.all(np.abs(W6 - W12) <= 16 * eps * np.maximum(u[4], W12))
+    assert np.mean(np.abs(W6 - W12) / W12) < 1e-15
+    assert np.mean(it6) < np.mean(it12)
