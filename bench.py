@@ -179,6 +179,7 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--wave", default="oblique", choices=["oblique", "x"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--guess", default="prev", choices=["prev", "cold", "mlp"])
     ap.add_argument("--ref-n", type=int, default=48)
     ap.add_argument("--cpu-n", type=int, default=64)
     ap.add_argument("--cpu-steps", type=int, default=2)
@@ -213,8 +214,12 @@ def main():
     n = args.n
     c, st = workload_state(n, args.wave)
     stream = torch.cuda.current_stream()
-    s = echo.Solver(n, n, n, precision=args.precision, device=local,
+    s = echo.Solver(n, n, n, precision=args.precision, device=local, guess=args.guess,
                     stream=stream.cuda_stream)
+    if args.guess == "mlp":
+        mk = lambda m: workload_state(m, args.wave)[1]
+        w, _ = harvest_and_train(64, 8, 4, mk, (1.0, 1.0, 1.0), 2401030081)
+        s.mlp_load(w)
     s.set_state(*st)
     s.step(args.warmup)
     torch.cuda.synchronize()

@@ -188,6 +188,7 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     for (int d = 0; d < 3; d++) g.inv_h[d] = 1.0 / g.h[d];
     g.hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
     g.gam = cfg->gamma_ad;
+    g.gfac = cfg->gamma_ad / (cfg->gamma_ad - 1.0);
     g.ho = cfg->ho;
     c->mixed = cfg->precision == ECHO_MIXED;
     if (cudaSetDevice(cfg->device) != cudaSuccess) {

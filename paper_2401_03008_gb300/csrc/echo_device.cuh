@@ -19,6 +19,7 @@ struct Grid {
     double inv_h[3];
     double hmin;
     double gam;        // adiabatic index
+    double gfac;       // gam / (gam - 1)
     int ho;            // high-order INT / DER
 };
 
@@ -387,12 +388,13 @@ __device__ __forceinline__ bool c2p_ok(const C2PInv &q, double W)
 // GB300).  Stops once a step is below 4e-6 W (FP32 cannot resolve much further);
 // returns the refined guess, or W0 unchanged if an iterate leaves the domain or
 // is not finite.  The FP64 iteration that follows decides the result.
-__device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &iters)
+__device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &iters, float &idf)
 {
     const float D = (float)q.D, S2 = (float)q.S2, B2 = (float)q.B2, SB = (float)q.SB;
     const float U = (float)q.U, gm1g = (float)q.gm1g, SB2 = SB * SB;
     float W = (float)W0;
     iters = 0;
+    idf = 0.f;
     if (!(W > 0.f) || !isfinite(W)) return W0;
     for (int k = 0; k < 8; k++) {
         float wb = W + B2;
@@ -409,11 +411,16 @@ __device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &ite
         float dp = gm1g * (omv2 - W * dv2 + 0.5f * D * dv2 * isq);
         float f = W - p + 0.5f * (1.f + v2) * B2 - 0.5f * SB2 * iW2 - U;
         float df = 1.f - dp + 0.5f * B2 * dv2 + SB2 * (iW2 * iW);
-        float dW = -f / df;
+        float rdf = 1.f / df;
+        float dW = -f * rdf;
         float Wn = W + dW;
         iters++;
-        if (!(Wn > 0.f) || !isfinite(Wn)) return W0;
+        if (!(Wn > 0.f) || !isfinite(Wn) || !isfinite(rdf)) {
+            idf = 0.f;
+            return W0;
+        }
         W = Wn;
+        idf = rdf;
         if (fabsf(dW) <= 4e-6f * W) break;
     }
     return (double)W;
@@ -438,7 +445,12 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     q.gm1g = (gam - 1.0) / gam;
     const double SB2 = q.SB * q.SB;
     iters32 = 0;
-    if (pre32) W0 = c2p_pre32(q, W0, iters32);
+    // mixed path: FP32 iterations first; their last derivative then serves every
+    // FP64 step (a chord iteration: FP64 residual, FP32-accurate slope, contraction
+    // by about the slope's relative error per step), so an FP64 step evaluates f only
+    float idf32 = 0.f;
+    if (pre32) W0 = c2p_pre32(q, W0, iters32, idf32);
+    const bool chord = idf32 != 0.f;
     double W = W0, v2 = 0.0, r = 0.0;
     bool ok = c2p_eval(q, W, v2, r);
     for (int k = 0; k < 64 && !ok; k++) {
@@ -455,11 +467,16 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
         double sq1 = omv2 * isq;
         double iW2 = iW * iW;
         double p = q.gm1g * (W * omv2 - q.D * sq1);
-        double dv2 = -2.0 * SB2 * (iW2 * iW) * iwb - 2.0 * v2 * iwb;
-        double dp = q.gm1g * (omv2 - W * dv2 + 0.5 * q.D * dv2 * isq);
         double f = W - p + 0.5 * (1.0 + v2) * q.B2 - 0.5 * SB2 * iW2 - q.U;
-        double df = 1.0 - dp + 0.5 * q.B2 * dv2 + SB2 * (iW2 * iW);
-        double dW = -f / df;
+        double dW;
+        if (chord) {
+            dW = -f * (double)idf32;
+        } else {
+            double dv2 = -2.0 * SB2 * (iW2 * iW) * iwb - 2.0 * v2 * iwb;
+            double dp = q.gm1g * (omv2 - W * dv2 + 0.5 * q.D * dv2 * isq);
+            double df = 1.0 - dp + 0.5 * q.B2 * dv2 + SB2 * (iW2 * iW);
+            dW = -f / df;
+        }
         if (!finite64(dW)) break;
         double lam = 1.0, Wn = W + dW, v2n, rn;
         bool okn = c2p_eval(q, Wn, v2n, rn);

@@ -52,10 +52,10 @@ k_init(Grid g, const double *__restrict__ prim5, const double *__restrict__ Bf,
     s[7] = int_c(Bz[shifted<2>(g, i, j, k, -2)], Bz[shifted<2>(g, i, j, k, -1)], Bz[c],
                  Bz[shifted<2>(g, i, j, k, 1)], g.ho);
     double u[8], f[8], lm, lp;
-    phys<double, 0>(s, g.gam, g.gam / (g.gam - 1.0), u, f, lm, lp);
+    phys<double, 0>(s, g.gam, g.gfac, u, f, lm, lp);
     for (int v = 0; v < 5; v++) U[v * n + c] = u[v];
     double v2 = s[1] * s[1] + s[2] * s[2] + s[3] * s[3];
-    W[c] = (s[0] + g.gam / (g.gam - 1.0) * s[4]) / (1.0 - v2);
+    W[c] = (s[0] + g.gfac * s[4]) / (1.0 - v2);
 }
 
 void launch_init(echo_ctx *c, const double *prim5)

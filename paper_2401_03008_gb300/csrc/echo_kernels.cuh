@@ -212,7 +212,7 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
         }
         if (nfb) atomicAdd(&sc->rec_fallbacks, (unsigned)nfb);
         const R gam = (R)g.gam;
-        const R gfac = (R)(g.gam / (g.gam - 1.0));
+        const R gfac = (R)g.gfac;
         R UL[8], FL[8], UR[8], FR[8], lmL, lpL, lmR, lpR;
         phys<R, D>(L, gam, gfac, UL, FL, lmL, lpL);
         phys<R, D>(Rt, gam, gfac, UR, FR, lmR, lpR);

@@ -82,7 +82,9 @@ __device__ __forceinline__ float mlp_warp_forward(const MlpDev &w, const float *
     const unsigned FULL = 0xffffffffu;
     const int g = lane >> 2, t = lane & 3;
     float ysel[2][2];
-#pragma unroll
+    // not unrolled: keeps the compiler from holding the first-layer weights of both
+    // m-tiles in registers at once
+#pragma unroll 1
     for (int mt = 0; mt < 2; mt++) {
         float xa[NIN], xb[NIN];
 #pragma unroll

@@ -189,6 +189,7 @@ echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, i
     for (int d = 0; d < 3; d++) g.inv_h[d] = 1.0 / g.h[d];
     g.hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
     g.gam = 0.0;
+    g.gfac = 0.0;
     g.ho = ho;
     cudaStream_t s = (cudaStream_t)stream;
     const int nblk = (int)((n + NA_THREADS - 1) / NA_THREADS);
