@@ -110,10 +110,12 @@ def dist_setup(args):
     return world, rank, local
 
 
-def workload_state(n, wave):
+def workload_state(n, wave, uct=1):
     from paper_2401_03008_gb300 import workloads as wl
     m = {"oblique": (1, 1, 1), "x": (1, 0, 0)}[wave]
     c = wl.CPA(n, n, n, m=m)
+    if not uct:
+        return c, (c.prim5(), c.bcell(), None)
     return c, (c.prim5(), c.bface_background(), c.apot())
 
 
@@ -148,8 +150,10 @@ def run_reference(args, world, rank):
 
 def workload_config(args):
     return {"workload": "relativistic circularly polarised Alfven wave, k along %s, "
-                        "%d^3 periodic, UCT + HO on, MP5, CFL 0.4, SSP-RK3"
-                        % ({"oblique": "(1,1,1)", "x": "x"}[args.wave], args.n),
+                        "%d^3 periodic, UCT %s, HO %s, MP5, CFL 0.4, SSP-RK3"
+                        % ({"oblique": "(1,1,1)", "x": "x"}[args.wave], args.n,
+                           "on" if getattr(args, "uct", 1) else "off",
+                           "on" if getattr(args, "ho", 1) else "off"),
             "cells": args.n ** 3, "precision": args.precision, "wave": args.wave,
             "l2_flush": "not needed: state of ~%.1f GB >> 129 MB L2" %
                         (args.n ** 3 * (472 if args.precision == "fp64" else 336) / 1e9),
@@ -180,6 +184,8 @@ def main():
     ap.add_argument("--wave", default="oblique", choices=["oblique", "x"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--guess", default="prev", choices=["prev", "cold", "mlp"])
+    ap.add_argument("--uct", type=int, default=1, help="0: cell-centred field, no UCT")
+    ap.add_argument("--ho", type=int, default=1, help="0: two-point INT and DER")
     ap.add_argument("--ref-n", type=int, default=48)
     ap.add_argument("--cpu-n", type=int, default=64)
     ap.add_argument("--cpu-steps", type=int, default=2)
@@ -212,10 +218,10 @@ def main():
             dist.barrier()
 
     n = args.n
-    c, st = workload_state(n, args.wave)
+    c, st = workload_state(n, args.wave, args.uct)
     stream = torch.cuda.current_stream()
     s = echo.Solver(n, n, n, precision=args.precision, device=local, guess=args.guess,
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, uct=args.uct, ho=args.ho)
     if args.guess == "mlp":
         mk = lambda m: workload_state(m, args.wave)[1]
         w, _ = harvest_and_train(64, 8, 4, mk, (1.0, 1.0, 1.0), 2401030081)
@@ -248,7 +254,8 @@ def main():
     value = world * n ** 3 * args.steps / (ms * 1e-3)
     diag = s.diagnostics()
     # FP64 state after warm-up + timed steps: the variants are compared with it
-    ref = s.primitives() if (args.variants and args.precision == "fp64") else None
+    ref = s.primitives() if (args.variants and args.precision == "fp64" and args.uct
+                             and args.ho) else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -72,7 +72,9 @@ typedef struct {
     double lx, ly, lz;  /* box lengths (> 0) */
     double gamma_ad;    /* adiabatic index of the ideal-gas law (Sec. 2, Eq. 6) */
     double cfl;         /* dt = cfl * min(h) / max fast speed (Sec. 3 step 5) */
-    int uct;            /* must be 1: staggered field evolved by UCT (Sec. 3) */
+    int uct;            /* 1: staggered field evolved by UCT (Sec. 3, Eq. 10); 0: the field is
+                           cell-centred like the other variables and all 8 components take
+                           the HLL flux (Sec. 3: UCT off; div B is then not preserved) */
     int ho;             /* 1: fourth-order INT and sixth-order DER; 0: two-point forms */
     int rec;            /* ECHO_REC_MP5 */
     int precision;      /* ECHO_FP64 or ECHO_MIXED */
@@ -97,10 +99,11 @@ echo_status echo_destroy(echo_ctx *ctx);
 
 /* Initial data (Sec. 4 and Sec. 5 set up the state from primitives and field).
  *   prim  [5][nz][ny][nx]: rho, vx, vy, vz, p at cell centres (required);
- *   bface [3][nz][ny][nx]: staggered field on faces (NULL: zero);
- *   apot  [3][nz][ny][nx]: edge vector potential (NULL: none); its discrete curl,
- *         with the same DER as the induction equation, is added to bface so that
- *         the discrete div B is zero to round-off.
+ *   bface [3][nz][ny][nx]: staggered field on faces (NULL: zero); with uct = 0 the
+ *         cell-centred field;
+ *   apot  [3][nz][ny][nx]: edge vector potential (NULL: none; uct = 1 only); its
+ *         discrete curl, with the same DER as the induction equation, is added to
+ *         bface so that the discrete div B is zero to round-off.
  * The conserved variables follow from the definitions of Sec. 2 (D = rho G,
  * S = rho h G^2 v + E x B, U = rho h G^2 - p + (E^2+B^2)/2, E = -v x B) with the
  * cell-centred field from INT.  Resets t and the step count to 0.  ECHO_ERR_ARG for

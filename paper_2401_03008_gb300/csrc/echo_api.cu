@@ -156,7 +156,7 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
         return fail(nullptr, ECHO_ERR_ARG, "box lengths must be > 0");
     if (!(cfg->gamma_ad > 1.0)) return fail(nullptr, ECHO_ERR_ARG, "gamma_ad must be > 1");
     if (!(cfg->cfl > 0.0)) return fail(nullptr, ECHO_ERR_ARG, "cfl must be > 0");
-    if (cfg->uct != 1) return fail(nullptr, ECHO_ERR_ARG, "only uct = 1 is built");
+    if (cfg->uct != 0 && cfg->uct != 1) return fail(nullptr, ECHO_ERR_ARG, "uct must be 0 or 1");
     if (cfg->ho != 0 && cfg->ho != 1) return fail(nullptr, ECHO_ERR_ARG, "ho must be 0 or 1");
     if (cfg->rec != ECHO_REC_MP5) return fail(nullptr, ECHO_ERR_ARG, "rec must be MP5");
     if (cfg->precision != ECHO_FP64 && cfg->precision != ECHO_MIXED)
@@ -190,6 +190,7 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     g.gam = cfg->gamma_ad;
     g.gfac = cfg->gamma_ad / (cfg->gamma_ad - 1.0);
     g.ho = cfg->ho;
+    g.uct = cfg->uct;
     c->mixed = cfg->precision == ECHO_MIXED;
     if (cudaSetDevice(cfg->device) != cudaSuccess) {
         delete c;
@@ -213,13 +214,16 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
         {(void **)&c->U, 5 * n * sizeof(double)},  {(void **)&c->U0, 5 * n * sizeof(double)},
         {(void **)&c->Bf, 3 * n * sizeof(double)}, {(void **)&c->Bf0, 3 * n * sizeof(double)},
         {(void **)&c->W, n * sizeof(double)},      {&c->prim, 8 * n * rs},
-        {&c->flux, 5 * n * rs},                    {&c->fdat[0], 6 * n * rs},
-        {&c->fdat[1], 6 * n * rs},                 {&c->fdat[2], 6 * n * rs},
-        {&c->E, 3 * n * rs},                       {&c->rhs, 5 * n * rs},
+        {&c->flux, (cfg->uct ? 5 : 8) * n * rs},
+        {&c->fdat[0], cfg->uct ? 6 * n * rs : 0},
+        {&c->fdat[1], cfg->uct ? 6 * n * rs : 0},
+        {&c->fdat[2], cfg->uct ? 6 * n * rs : 0},
+        {&c->E, cfg->uct ? 3 * n * rs : 0},
+        {&c->rhs, (cfg->uct ? 5 : 8) * n * rs},
         {(void **)&c->sc, sizeof(DevScalars)},
         {(void **)&c->partials, echo::DIAG_BLOCKS * echo::DIAG_Q * sizeof(double)},
         {(void **)&c->dres, 32 * sizeof(double)},
-        {(void **)&c->Bf32, c->mixed ? 3 * n * sizeof(float) : 0},
+        {(void **)&c->Bf32, c->mixed && cfg->uct ? 3 * n * sizeof(float) : 0},
     };
     for (auto &a : al) {
         if (a.bytes == 0) continue;
@@ -271,6 +275,8 @@ echo_status echo_set_state(echo_ctx *c, const double *prim, const double *bface,
     } else {
         CK(cudaMemsetAsync(c->Bf, 0, 3 * n * sizeof(double), c->stream));
     }
+    if (apot && !c->g.uct)
+        return fail(c, ECHO_ERR_ARG, "apot needs the staggered field (uct = 1)");
     if (apot) {
         const double *da;
         if ((st = input(c, apot, 3 * n, ptr_kind, 0, &da))) return st;
@@ -426,18 +432,40 @@ echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *am
         dc = c->stage8;
         df = c->stage8 + 5 * n;
     }
+    // with UCT off the rhs holds 8 components: cells [0..4], field [5..7]
+    double *tmp8 = nullptr;
+    if (!c->g.uct) {
+        if ((st = ensure_stage(c))) return st;
+        tmp8 = c->stage8;  // 8n of the 9n staging doubles
+        if (ptr_kind != ECHO_PTR_DEVICE) {
+            dc = c->stage8;
+            df = c->stage8 + 5 * n;
+        }
+    }
     if (c->mixed) {
         Path<float>::int_c2p(c, 0, -1, 1);
         Path<float>::sweeps(c, 1);
         Path<float>::uct(c);
-        if (df) Path<float>::curl_out(c, df);
-        if (dc) Path<float>::rhs_out(c, dc);
+        if (c->g.uct) {
+            if (df) Path<float>::curl_out(c, df);
+            if (dc) Path<float>::rhs_out(c, dc);
+        } else {
+            Path<float>::rhs_out(c, tmp8);
+        }
     } else {
         Path<double>::int_c2p(c, 0, -1, 1);
         Path<double>::sweeps(c, 1);
         Path<double>::uct(c);
-        if (df) Path<double>::curl_out(c, df);
-        if (dc) Path<double>::rhs_out(c, dc);
+        if (c->g.uct) {
+            if (df) Path<double>::curl_out(c, df);
+            if (dc) Path<double>::rhs_out(c, dc);
+        } else {
+            Path<double>::rhs_out(c, tmp8);
+        }
+    }
+    if (!c->g.uct && ptr_kind == ECHO_PTR_DEVICE) {
+        if (dc) CK(cudaMemcpyAsync(dc, tmp8, 5 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        if (df) CK(cudaMemcpyAsync(df, tmp8 + 5 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
     if ((st = sync_check(c))) return st;
     if ((st = read_sc(c, &h))) return st;

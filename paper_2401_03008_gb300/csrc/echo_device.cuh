@@ -21,7 +21,9 @@ struct Grid {
     double gam;        // adiabatic index
     double gfac;       // gam / (gam - 1)
     int ho;            // high-order INT / DER
+    int uct;           // 1: staggered field + UCT; 0: cell-centred field, 8-component HLL
 };
+
 
 // Device-side scalars of the time loop and the health counters.
 struct DevScalars {
@@ -243,6 +245,31 @@ __device__ __forceinline__ R int_c(R a, R b, R c, R d, int ho)
 {
     if (ho) return (-a + R(9) * b + R(9) * c - d) * R(0.0625);
     return R(0.5) * (b + c);
+}
+
+// cell-centred field at cell c: INT of the staggered components (UCT) or the cell
+// values themselves (UCT off)
+template <typename BT>
+__device__ __forceinline__ double cell_field(const Grid &g, const BT *__restrict__ Bf, long c,
+                                             int i, int j, int k, int d)
+{
+    const BT *b = Bf + d * g.n;
+    if (!g.uct) return (double)b[c];
+    long sm2, sm1, sp1;
+    if (d == 0) {
+        sm2 = lin(g, wrapi(i - 2, g.nx), j, k);
+        sm1 = lin(g, wrapi(i - 1, g.nx), j, k);
+        sp1 = lin(g, wrapi(i + 1, g.nx), j, k);
+    } else if (d == 1) {
+        sm2 = lin(g, i, wrapi(j - 2, g.ny), k);
+        sm1 = lin(g, i, wrapi(j - 1, g.ny), k);
+        sp1 = lin(g, i, wrapi(j + 1, g.ny), k);
+    } else {
+        sm2 = lin(g, i, j, wrapi(k - 2, g.nz));
+        sm1 = lin(g, i, j, wrapi(k - 1, g.nz));
+        sp1 = lin(g, i, j, wrapi(k + 1, g.nz));
+    }
+    return (double)int_c(b[sm2], b[sm1], b[c], b[sp1], g.ho);
 }
 
 // DER: derivative at a centre from staggered values s[0..5] at i-5/2..i+5/2.

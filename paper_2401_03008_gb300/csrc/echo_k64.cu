@@ -44,13 +44,8 @@ k_init(Grid g, const double *__restrict__ prim5, const double *__restrict__ Bf,
     coords(g, c, i, j, k);
     double s[8];
     for (int v = 0; v < 5; v++) s[v] = prim5[v * n + c];
-    s[5] = int_c(Bf[shifted<0>(g, i, j, k, -2)], Bf[shifted<0>(g, i, j, k, -1)], Bf[c],
-                 Bf[shifted<0>(g, i, j, k, 1)], g.ho);
-    const double *By = Bf + n, *Bz = Bf + 2 * n;
-    s[6] = int_c(By[shifted<1>(g, i, j, k, -2)], By[shifted<1>(g, i, j, k, -1)], By[c],
-                 By[shifted<1>(g, i, j, k, 1)], g.ho);
-    s[7] = int_c(Bz[shifted<2>(g, i, j, k, -2)], Bz[shifted<2>(g, i, j, k, -1)], Bz[c],
-                 Bz[shifted<2>(g, i, j, k, 1)], g.ho);
+#pragma unroll
+    for (int d = 0; d < 3; d++) s[5 + d] = cell_field(g, Bf, c, i, j, k, d);
     double u[8], f[8], lm, lp;
     phys<double, 0>(s, g.gam, g.gfac, u, f, lm, lp);
     for (int v = 0; v < 5; v++) U[v * n + c] = u[v];

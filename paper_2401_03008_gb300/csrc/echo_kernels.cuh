@@ -44,13 +44,8 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
         int i, j, k;
         coords(g, c, i, j, k);
         double B[3];
-        B[0] = int_c(Bf[shifted<0>(g, i, j, k, -2)], Bf[shifted<0>(g, i, j, k, -1)],
-                     Bf[c], Bf[shifted<0>(g, i, j, k, 1)], g.ho);
-        const double *By = Bf + n, *Bz = Bf + 2 * n;
-        B[1] = int_c(By[shifted<1>(g, i, j, k, -2)], By[shifted<1>(g, i, j, k, -1)],
-                     By[c], By[shifted<1>(g, i, j, k, 1)], g.ho);
-        B[2] = int_c(Bz[shifted<2>(g, i, j, k, -2)], Bz[shifted<2>(g, i, j, k, -1)],
-                     Bz[c], Bz[shifted<2>(g, i, j, k, 1)], g.ho);
+#pragma unroll
+        for (int d = 0; d < 3; d++) B[d] = cell_field(g, Bf, c, i, j, k, d);
         double u[5];
 #pragma unroll
         for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
@@ -125,12 +120,7 @@ k_mlp_guess(Grid g, const double *__restrict__ U, const BT *__restrict__ Bf,
         if (c < n) {
             int i, j, k;
             coords(g, c, i, j, k);
-            for (int d = 0; d < 3; d++) {
-                const BT *b = Bf + d * n;
-                B[d] = (double)int_c(__ldg(b + shifted_rt(g, i, j, k, d, -2)),
-                                     __ldg(b + shifted_rt(g, i, j, k, d, -1)), __ldg(b + c),
-                                     __ldg(b + shifted_rt(g, i, j, k, d, 1)), g.ho);
-            }
+            for (int d = 0; d < 3; d++) B[d] = cell_field(g, Bf, c, i, j, k, d);
             for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
         }
         float x[NIN];
@@ -152,10 +142,11 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
        R *__restrict__ fd, DevScalars *sc, int want_amax)
 {
     if (sc->halt) return;
-    __shared__ Mp5Queue<R, 14, QMAX, BS> q;
+    __shared__ Mp5Queue<R, 16, QMAX, BS> q;
     q.reset();
     __syncthreads();
     const long n = g.n;
+    const int uct = g.uct;
     long f = blockIdx.x * (long)BS + threadIdx.x;
     const bool active = f < n;
     R amax = R(0);
@@ -169,13 +160,13 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
         for (int m = 0; m < 6; m++) cs[m] = shifted<D>(g, i, j, k, m - 2);
 #pragma unroll
         for (int v = 0; v < 8; v++) {
-            if (v == 5 + D) continue;
-            const int vi = v < 5 + D ? v : v - 1;  // 0..6 over the reconstructed variables
+            // with UCT the normal field is the staggered face value, not reconstructed
+            if (v == 5 + D && uct) continue;
             R s[6];
 #pragma unroll
             for (int m = 0; m < 6; m++) s[m] = ld(prim + v * n + cs[m]);
-            L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], 2 * vi, mask);
-            Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], 2 * vi + 1, mask);
+            L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], 2 * v, mask);
+            Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], 2 * v + 1, mask);
         }
     }
     __syncthreads();
@@ -184,14 +175,14 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
     if (active) {
 #pragma unroll
         for (int v = 0; v < 8; v++) {
-            if (v == 5 + D) continue;
-            const int vi = v < 5 + D ? v : v - 1;
-            if (mask & (1u << (2 * vi))) L[v] = q.get(2 * vi);
-            if (mask & (1u << (2 * vi + 1))) Rt[v] = q.get(2 * vi + 1);
+            if (mask & (1u << (2 * v))) L[v] = q.get(2 * v);
+            if (mask & (1u << (2 * v + 1))) Rt[v] = q.get(2 * v + 1);
         }
-        const R bn = Bf[D * n + f];
-        L[5 + D] = bn;
-        Rt[5 + D] = bn;
+        if (uct) {
+            const R bn = Bf[D * n + f];
+            L[5 + D] = bn;
+            Rt[5 + D] = bn;
+        }
         // positivity: reset a state to the first-order (cell) value
         int nfb = 0;
         {
@@ -199,14 +190,14 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
             if (!gtz(L[0]) || !gtz(L[4]) || !lt(v2, R(1))) {
 #pragma unroll
                 for (int v = 0; v < 8; v++)
-                    if (v != 5 + D) L[v] = prim[v * n + cs[2]];
+                    if (v != 5 + D || !uct) L[v] = prim[v * n + cs[2]];
                 nfb++;
             }
             v2 = Rt[1] * Rt[1] + Rt[2] * Rt[2] + Rt[3] * Rt[3];
             if (!gtz(Rt[0]) || !gtz(Rt[4]) || !lt(v2, R(1))) {
 #pragma unroll
                 for (int v = 0; v < 8; v++)
-                    if (v != 5 + D) Rt[v] = prim[v * n + cs[3]];
+                    if (v != 5 + D || !uct) Rt[v] = prim[v * n + cs[3]];
                 nfb++;
             }
         }
@@ -219,22 +210,27 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
         R ap = rmax(R(0), rmax(lpL, lpR));
         R am = rmax(R(0), rmax(-lmL, -lmR));
         R s = ap + am;
+        const int ncomp = uct ? 5 : 8;  // with UCT the field takes the edge fields instead
         if (gtz(s)) {
             R is = R(1) / s;
 #pragma unroll
-            for (int qq = 0; qq < 5; qq++)
-                flux[qq * n + f] = (ap * FL[qq] + am * FR[qq] - ap * am * (UR[qq] - UL[qq])) * is;
+            for (int qq = 0; qq < 8; qq++)
+                if (qq < ncomp)
+                    flux[qq * n + f] = (ap * FL[qq] + am * FR[qq] - ap * am * (UR[qq] - UL[qq])) * is;
         } else {
 #pragma unroll
-            for (int qq = 0; qq < 5; qq++) flux[qq * n + f] = R(0.5) * (FL[qq] + FR[qq]);
+            for (int qq = 0; qq < 8; qq++)
+                if (qq < ncomp) flux[qq * n + f] = R(0.5) * (FL[qq] + FR[qq]);
         }
-        constexpr int E1 = (D + 1) % 3;
-        fd[f] = L[1 + D];
-        fd[n + f] = L[1 + E1];
-        fd[2 * n + f] = Rt[1 + D];
-        fd[3 * n + f] = Rt[1 + E1];
-        fd[4 * n + f] = ap;
-        fd[5 * n + f] = am;
+        if (uct) {
+            constexpr int E1 = (D + 1) % 3;
+            fd[f] = L[1 + D];
+            fd[n + f] = L[1 + E1];
+            fd[2 * n + f] = Rt[1 + D];
+            fd[3 * n + f] = Rt[1 + E1];
+            fd[4 * n + f] = ap;
+            fd[5 * n + f] = am;
+        }
         amax = rmax(ap, am);
     }
     if (want_amax) {
@@ -270,8 +266,10 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
 #pragma unroll
     for (int m = 0; m < 6; m++) fs[m] = shifted<D>(g, i, j, k, m - 3);
     const R ih = (R)g.inv_h[D];
+    const int ncomp = g.uct ? 5 : 8;
 #pragma unroll
-    for (int q = 0; q < 5; q++) {
+    for (int q = 0; q < 8; q++) {
+        if (q >= ncomp) break;
         R s[6];
 #pragma unroll
         for (int m = 0; m < 6; m++) s[m] = ld(flux + q * n + fs[m]);
@@ -386,7 +384,7 @@ k_rk(Grid g, int stage, const R *__restrict__ E, const R *__restrict__ rhs,
                 pu = U + v * n + c;
                 pu0 = U0 + v * n + c;
             } else {
-                r = -(double)curl_a(g, E, v - 5, i, j, k);
+                r = g.uct ? -(double)curl_a(g, E, v - 5, i, j, k) : (double)rhs[v * n + c];
                 pu = Bf + (v - 5) * n + c;
                 pu0 = Bf0 + (v - 5) * n + c;
             }
@@ -483,6 +481,7 @@ void Path<R>::sweeps(echo_ctx *c, int want_amax)
 template <typename R>
 void Path<R>::uct(echo_ctx *c)
 {
+    if (!c->g.uct) return;
     const unsigned nb = nblocks(c->g.n, BS);
     const R *f0 = (const R *)c->fdat[0], *f1 = (const R *)c->fdat[1], *f2 = (const R *)c->fdat[2];
     const R *bf = face_field<R>(c);
@@ -508,7 +507,7 @@ void Path<R>::curl_out(echo_ctx *c, double *out)
 template <typename R>
 void Path<R>::rhs_out(echo_ctx *c, double *out)
 {
-    long m = 5 * c->g.n;
+    long m = (c->g.uct ? 5 : 8) * c->g.n;
     launch(c, K_MISC, k_to_double<R>, nblocks(m, BS), BS, 0, m, (const R *)c->rhs, out);
 }
 

@@ -73,11 +73,7 @@ k_mlp_harvest(Grid g, const double *__restrict__ U, const double *__restrict__ B
     int i, j, k;
     coords(g, c, i, j, k);
     double B[3];
-    for (int d = 0; d < 3; d++) {
-        const double *b = Bf + d * n;
-        B[d] = int_c(b[shifted_rt(g, i, j, k, d, -2)], b[shifted_rt(g, i, j, k, d, -1)], b[c],
-                     b[shifted_rt(g, i, j, k, d, 1)], g.ho);
-    }
+    for (int d = 0; d < 3; d++) B[d] = cell_field(g, Bf, c, i, j, k, d);
     double u[5];
     for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
     float x[NIN];

@@ -143,7 +143,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, L=(1.0, 1.0, 1.0), gamma=4.0 / 3.0, cfl=0.4, ho=1,
                  precision="fp64", guess="prev", tol=1e-6, maxit=100, device=0,
-                 stream=None):
+                 stream=None, uct=1):
         self.L = lib()
         cfg = Config()
         self.L.echo_config_default(C.byref(cfg))
@@ -152,6 +152,7 @@ class Solver:
         cfg.gamma_ad = gamma
         cfg.cfl = cfl
         cfg.ho = ho
+        cfg.uct = uct
         cfg.precision = {"fp64": FP64, "mixed": MIXED}[precision]
         cfg.c2p_guess = {"prev": GUESS_PREV, "cold": GUESS_COLD, "mlp": GUESS_MLP}[guess]
         cfg.c2p_tol = tol

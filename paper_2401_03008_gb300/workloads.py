@@ -112,6 +112,11 @@ class CPA:
             out[c] = amp * (self.Y[c] * np.cos(xi) + self.Z[c] * np.sin(xi))
         return out
 
+    def bcell(self, t=0.0):
+        """[3, nz, ny, nx]: the exact field at cell centres (for the cell-centred
+        variant without constrained transport)."""
+        return np.ascontiguousarray(self.exact_prim8(t)[5:8])
+
     def exact_prim8(self, t):
         """[8, nz, ny, nx]: exact rho, v, p and B at cell centres at time t."""
         nx, ny, nz = self.n
@@ -288,6 +293,7 @@ class Turbulence:
         c = (0.5, 0.5, 0.5)
         dB = np.array([_synth(n, self.modes, kxe_B[:, q], self.phB, c) for q in range(3)])
         self.aB = eta_b * self.B0 / np.mean(np.sqrt(np.sum(dB ** 2, axis=0)))
+        self._dBc = dB * self.aB
         u = np.array([_synth(n, self.modes, kxe_u[:, q], self.phu, c) for q in range(3)])
         umax = np.max(np.sqrt(np.sum(u ** 2, axis=0)))
         self.au = math.sqrt(lorentz_max ** 2 - 1.0) / umax
@@ -307,6 +313,13 @@ class Turbulence:
         out = np.zeros((3, n, n, n))
         out[2] = self.B0
         return out
+
+    def bcell(self):
+        """[3, n, n, n]: the field at cell centres (B0 z + delta B), for the cell-centred
+        variant without constrained transport."""
+        out = self._dBc.copy()
+        out[2] += self.B0
+        return np.ascontiguousarray(out)
 
     def apot(self):
         """Edge vector potential: A_x at (i, j+1/2, k+1/2) and cyclic."""

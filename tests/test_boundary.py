@@ -39,7 +39,7 @@ def test_config_default():
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("lz", -1.0), ("gamma_ad", 1.0),
-                                         ("cfl", 0.0), ("uct", 0), ("ho", 2), ("precision", 7),
+                                         ("cfl", 0.0), ("uct", 2), ("ho", 2), ("precision", 7),
                                          ("c2p_guess", 5), ("c2p_maxit", 0)])
 def test_create_rejects_bad_config(field, value):
     L = echo.lib()

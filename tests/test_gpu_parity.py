@@ -281,3 +281,43 @@ def test_fma_probe_plausible():
     f64 = s.probe_fma_peak("fp64")
     f32 = s.probe_fma_peak("fp32")
     assert 1e11 < f64 < 1e14 and 1e13 < f32 < 1e15
+
+
+@pytest.mark.parametrize("ho", [0, 1])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cell_centred_variant_parity(ho, precision):
+    """UCT off: the field is cell-centred and all 8 components take the HLL flux."""
+    n = (24, 20, 16)
+    c = wl.CPA(*n, m=(1, 1, 1))
+    st = (c.prim5(), c.bcell(), None)
+    g = orc.Grid(*n, uct=0, ho=ho)
+    g.set_state(*st)
+    s = echo.Solver(*n, ho=ho, uct=0, precision=precision)
+    s.set_state(*st)
+    cons0 = g.cons.copy()
+    rc, rb, amax, bad = g.rhs()
+    grc, grb, gamax = s.rhs()
+    if precision == "fp64":
+        hmin = 1.0 / 24
+        for got, ref, q, groups in ((grc, rc, cons0, CONS_GROUPS), (grb, rb, g.bf, FACE_GROUPS)):
+            for grp in groups:
+                floor = np.max(np.abs(q[grp])) * amax / hmin
+                assert_parity(got[grp], ref[grp], [list(range(len(grp)))], floor=floor)
+    g.step(5)
+    s.step(5)
+    tol = FP64_TOL if precision == "fp64" else 1e-5
+    assert_parity(s.primitives(), g.primitives(), PRIM_GROUPS, tol=tol, what="uct off")
+
+
+def test_cell_centred_turbulence_parity():
+    n = 20
+    tb = wl.Turbulence(n, seed=105, lorentz_max=2.0)
+    st = (tb.prim5(), tb.bcell(), None)
+    L = (2 * np.pi,) * 3
+    g = orc.Grid(n, n, n, *L, uct=0, ho=0)
+    g.set_state(*st)
+    s = echo.Solver(n, n, n, L=L, uct=0, ho=0)
+    s.set_state(*st)
+    g.step(4)
+    s.step(4)
+    assert_parity(s.primitives(), g.primitives(), PRIM_GROUPS, what="turbulence, uct off")
