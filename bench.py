@@ -150,10 +150,12 @@ def run_reference(args, world, rank):
 
 def workload_config(args):
     return {"workload": "relativistic circularly polarised Alfven wave, k along %s, "
-                        "%d^3 periodic, UCT %s, HO %s, MP5, CFL 0.4, SSP-RK3"
+                        "%d^3 periodic, UCT %s, HO %s, %s, CFL 0.4, SSP-RK%d"
                         % ({"oblique": "(1,1,1)", "x": "x"}[args.wave], args.n,
                            "on" if getattr(args, "uct", 1) else "off",
-                           "on" if getattr(args, "ho", 1) else "off"),
+                           "on" if getattr(args, "ho", 1) else "off",
+                           "MP5" if getattr(args, "rec", "mp5") == "mp5" else "linear (MC)",
+                           getattr(args, "rk", 3)),
             "cells": args.n ** 3, "precision": args.precision, "wave": args.wave,
             "l2_flush": "not needed: state of ~%.1f GB >> 129 MB L2" %
                         (args.n ** 3 * (472 if args.precision == "fp64" else 336) / 1e9),
@@ -186,6 +188,8 @@ def main():
     ap.add_argument("--guess", default="prev", choices=["prev", "cold", "mlp"])
     ap.add_argument("--uct", type=int, default=1, help="0: cell-centred field, no UCT")
     ap.add_argument("--ho", type=int, default=1, help="0: two-point INT and DER")
+    ap.add_argument("--rec", default="mp5", choices=["mp5", "linear"])
+    ap.add_argument("--rk", type=int, default=3, choices=[2, 3])
     ap.add_argument("--ref-n", type=int, default=48)
     ap.add_argument("--cpu-n", type=int, default=64)
     ap.add_argument("--cpu-steps", type=int, default=2)
@@ -221,7 +225,8 @@ def main():
     c, st = workload_state(n, args.wave, args.uct)
     stream = torch.cuda.current_stream()
     s = echo.Solver(n, n, n, precision=args.precision, device=local, guess=args.guess,
-                    stream=stream.cuda_stream, uct=args.uct, ho=args.ho)
+                    stream=stream.cuda_stream, uct=args.uct, ho=args.ho, rec=args.rec,
+                    rk_order=args.rk)
     if args.guess == "mlp":
         mk = lambda m: workload_state(m, args.wave)[1]
         w, _ = harvest_and_train(64, 8, 4, mk, (1.0, 1.0, 1.0), 2401030081)
@@ -255,7 +260,7 @@ def main():
     diag = s.diagnostics()
     # FP64 state after warm-up + timed steps: the variants are compared with it
     ref = s.primitives() if (args.variants and args.precision == "fp64" and args.uct
-                             and args.ho) else None
+                             and args.ho and args.rec == "mp5" and args.rk == 3) else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

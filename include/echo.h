@@ -54,7 +54,10 @@ typedef enum {
 } echo_status;
 
 enum { ECHO_PTR_HOST = 0, ECHO_PTR_DEVICE = 1 };
-enum { ECHO_REC_MP5 = 0 };
+/* ECHO_REC_MP5: the five-point MP5 scheme (Sec. 3); ECHO_REC_LINEAR: linear
+ * reconstruction with the monotonized-central limiter (the faster variant of Sec. 4,
+ * usually with rk_order = 2). */
+enum { ECHO_REC_MP5 = 0, ECHO_REC_LINEAR = 1 };
 /* ECHO_FP64: every step in double precision.  ECHO_MIXED: reconstruction, fluxes,
  * HLL, DER and the UCT fields in single precision; the inversion (Lorentz factor and
  * pressure recovery included) and the Runge-Kutta accumulation of the conserved
@@ -76,17 +79,18 @@ typedef struct {
                            cell-centred like the other variables and all 8 components take
                            the HLL flux (Sec. 3: UCT off; div B is then not preserved) */
     int ho;             /* 1: fourth-order INT and sixth-order DER; 0: two-point forms */
-    int rec;            /* ECHO_REC_MP5 */
+    int rec;            /* ECHO_REC_MP5 or ECHO_REC_LINEAR (also used inside UCT) */
     int precision;      /* ECHO_FP64 or ECHO_MIXED */
     int c2p_guess;      /* ECHO_GUESS_* */
     double c2p_tol;     /* Newton stop: an undamped step |dW| <= tol W, then one polishing step */
     int c2p_maxit;      /* Newton iteration cap (a cell past it is a failure) */
     int device;         /* CUDA device ordinal */
     void *stream;       /* cudaStream_t to launch on; NULL: the library makes one */
+    int rk_order;       /* 3: SSP-RK3 (default); 2: SSP-RK2 (the faster variant of Sec. 4) */
 } echo_config;
 
 /* Fill *cfg with defaults: 32^3 unit box, gamma 4/3, cfl 0.4, uct 1, ho 1, MP5,
- * FP64, previous-W guess, tol 1e-6, maxit 100, device 0, own stream. */
+ * FP64, previous-W guess, tol 1e-6, maxit 100, device 0, own stream, SSP-RK3. */
 echo_status echo_config_default(echo_config *cfg);
 
 /* Validate cfg, select its device, allocate the device state (library-owned) and
@@ -111,7 +115,7 @@ echo_status echo_destroy(echo_ctx *ctx);
 echo_status echo_set_state(echo_ctx *ctx, const double *prim, const double *bface,
                            const double *apot, int ptr_kind);
 
-/* Advance by SSP-RK3 steps (Sec. 3, steps 1-5) until max_steps steps are done or
+/* Advance by Runge-Kutta steps (SSP-RK3, or SSP-RK2 with rk_order = 2; Sec. 3, steps 1-5) until max_steps steps are done or
  * t reaches t_end (the last step is shortened to land on t_end; pass
  * INFINITY for no limit).  *steps_done and *t_now (either may be NULL) receive
  * the steps taken and the time reached.  On ECHO_ERR_C2P or ECHO_ERR_NONFINITE the

@@ -48,6 +48,8 @@ typedef struct {
     int maxit;           /* Newton iteration cap */
     int guess;           /* 0: previous W (warm), 1: W0 = U (cold), 2: caller array */
     int nthreads;        /* OpenMP threads (0: library default) */
+    int rec;             /* 0: MP5; 1: linear with the MC limiter */
+    int rk;              /* Runge-Kutta order: 3 (SSP-RK3) or 2 (SSP-RK2) */
 } orc_cfg;
 
 typedef struct {
@@ -261,6 +263,22 @@ double orc_mp5(const double *s)
     return uor + minmod2(umin - uor, umax - uor);
 }
 
+/* Linear reconstruction (Sec. 4, last paragraph: the faster variant uses linear
+ * reconstruction instead of MP5; the limiter is not named there).  Monotonized-
+ * central slope of cell i from (u_{i-1}, u_i, u_{i+1}):
+ * minmod(2 (u_i - u_{i-1}), (u_{i+1} - u_{i-1})/2, 2 (u_{i+1} - u_i)); the value at
+ * i+1/2 is u_i + slope/2. */
+static double mc_slope(double um1, double u0, double up1)
+{
+    double a = 2.0 * (u0 - um1), b = 0.5 * (up1 - um1), c = 2.0 * (up1 - u0);
+    if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+    if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+    return 0.0;
+}
+
+/* value at i+1/2 from s = (u_{i-1}, u_i, u_{i+1}) */
+double orc_mc(const double *s) { return s[1] + 0.5 * mc_slope(s[0], s[1], s[2]); }
+
 /* Right-biased MP5 state at i+1/2: the mirror stencil (u_{i+3}, ..., u_{i-1}). */
 static double mp5_right(const double *s6)
 {
@@ -269,6 +287,22 @@ static double mp5_right(const double *s6)
 }
 
 static double mp5_left(const double *s6) { return orc_mp5(s6); }
+
+/* left and right states at i+1/2 from s6 = (u_{i-2}, ..., u_{i+3}) with the
+ * configured reconstruction */
+static double rec_left(const orc_cfg *g, const double *s6)
+{
+    return g->rec == 1 ? orc_mc(s6 + 1) : mp5_left(s6);
+}
+
+static double rec_right(const orc_cfg *g, const double *s6)
+{
+    if (g->rec == 1) {
+        double m[3] = {s6[4], s6[3], s6[2]};
+        return orc_mc(m);
+    }
+    return mp5_right(s6);
+}
 
 /* INT (Sec. 3 step 1): staggered value to the cell centre along its own direction,
  * from faces (i-3/2, i-1/2, i+1/2, i+3/2) in s.  Second order: mean of the two
@@ -527,8 +561,8 @@ static int face_states(const orc_cfg *g, const double *prim, const double *bf, i
     for (int v = 0; v < 8; v++) {
         double s6[6];
         for (int m = 0; m < 6; m++) s6[m] = prim[v * n + at(g, i, j, k, d, m - 2)];
-        L[v] = mp5_left(s6);
-        R[v] = mp5_right(s6);
+        L[v] = rec_left(g, s6);
+        R[v] = rec_right(g, s6);
     }
     if (g->uct) L[5 + d] = R[5 + d] = bf[d * n + at(g, i, j, k, d, 0)];
     int nfb = 0;
@@ -614,19 +648,19 @@ static void uct_edges(const orc_cfg *g, const double *bf, int c, double *const *
                 for (int s = 0; s < 2; s++) {
                     for (int m = 0; m < 6; m++)
                         s6[m] = fvel[a][(2 * s + 0) * n + at(g, i, j, k, b, m - 2)];
-                    va[s][0] = mp5_left(s6);
-                    va[s][1] = mp5_right(s6);
+                    va[s][0] = rec_left(g, s6);
+                    va[s][1] = rec_right(g, s6);
                     for (int m = 0; m < 6; m++)
                         s6[m] = fvel[a][(2 * s + 1) * n + at(g, i, j, k, b, m - 2)];
-                    vb[s][0] = mp5_left(s6);
-                    vb[s][1] = mp5_right(s6);
+                    vb[s][0] = rec_left(g, s6);
+                    vb[s][1] = rec_right(g, s6);
                 }
                 for (int m = 0; m < 6; m++) s6[m] = bf[a * n + at(g, i, j, k, b, m - 2)];
-                Ba[0] = mp5_left(s6);
-                Ba[1] = mp5_right(s6);
+                Ba[0] = rec_left(g, s6);
+                Ba[1] = rec_right(g, s6);
                 for (int m = 0; m < 6; m++) s6[m] = bf[b * n + at(g, i, j, k, a, m - 2)];
-                Bb[0] = mp5_left(s6);
-                Bb[1] = mp5_right(s6);
+                Bb[0] = rec_left(g, s6);
+                Bb[1] = rec_right(g, s6);
                 long e0 = at(g, i, j, k, 0, 0);
                 long ea1 = at(g, i, j, k, b, 1); /* a-face one step up along b */
                 long eb1 = at(g, i, j, k, a, 1); /* b-face one step up along a */
@@ -765,11 +799,12 @@ void orc_set_state(const orc_cfg *g, const double *prim5, const double *bf,
     free(bc);
 }
 
-/* Step 5: one SSP-RK3 step in Shu-Osher form (the paper uses Runge-Kutta
+/* Step 5: one Runge-Kutta step in Shu-Osher form (the paper uses Runge-Kutta
  * substeps, Sec. 3 step 5; the third-order strong-stability-preserving scheme is
- * the one run here):
- *   U1 = Un + dt L(Un); U2 = 3/4 Un + 1/4 (U1 + dt L(U1));
- *   U(n+1) = 1/3 Un + 2/3 (U2 + dt L(U2)).
+ * the default, the second-order one serves the faster variant of Sec. 4):
+ *   SSP-RK3: U1 = Un + dt L(Un); U2 = 3/4 Un + 1/4 (U1 + dt L(U1));
+ *            U(n+1) = 1/3 Un + 2/3 (U2 + dt L(U2)).
+ *   SSP-RK2: U1 = Un + dt L(Un); U(n+1) = 1/2 Un + 1/2 (U1 + dt L(U1)).
  * dt = cfl * min(h) / max(a+, a-) over all faces of the first substep, cut so
  * that t does not pass t_end.  Returns 0, or 1 if any C2P failed. */
 int orc_step(const orc_cfg *g, double *cons, double *bf, double *W, const double *guessarr,
@@ -790,13 +825,18 @@ int orc_step(const orc_cfg *g, double *cons, double *bf, double *W, const double
     for (long q = 0; q < nc; q++) cons[q] = u0[q] + dt * rc[q];
     for (long q = 0; q < nb; q++) bf[q] = b0[q] + dt * rb[q];
     bad |= orc_rhs(g, cons, bf, W, guessarr, rc, rb, NULL, NULL, st);
-    for (long q = 0; q < nc; q++) cons[q] = 0.75 * u0[q] + 0.25 * (cons[q] + dt * rc[q]);
-    for (long q = 0; q < nb; q++) bf[q] = 0.75 * b0[q] + 0.25 * (bf[q] + dt * rb[q]);
-    bad |= orc_rhs(g, cons, bf, W, guessarr, rc, rb, NULL, NULL, st);
-    for (long q = 0; q < nc; q++)
-        cons[q] = u0[q] / 3.0 + 2.0 / 3.0 * (cons[q] + dt * rc[q]);
-    for (long q = 0; q < nb; q++)
-        bf[q] = b0[q] / 3.0 + 2.0 / 3.0 * (bf[q] + dt * rb[q]);
+    if (g->rk == 2) {
+        for (long q = 0; q < nc; q++) cons[q] = 0.5 * u0[q] + 0.5 * (cons[q] + dt * rc[q]);
+        for (long q = 0; q < nb; q++) bf[q] = 0.5 * b0[q] + 0.5 * (bf[q] + dt * rb[q]);
+    } else {
+        for (long q = 0; q < nc; q++) cons[q] = 0.75 * u0[q] + 0.25 * (cons[q] + dt * rc[q]);
+        for (long q = 0; q < nb; q++) bf[q] = 0.75 * b0[q] + 0.25 * (bf[q] + dt * rb[q]);
+        bad |= orc_rhs(g, cons, bf, W, guessarr, rc, rb, NULL, NULL, st);
+        for (long q = 0; q < nc; q++)
+            cons[q] = u0[q] / 3.0 + 2.0 / 3.0 * (cons[q] + dt * rc[q]);
+        for (long q = 0; q < nb; q++)
+            bf[q] = b0[q] / 3.0 + 2.0 / 3.0 * (bf[q] + dt * rb[q]);
+    }
     *t += dt;
     if (dt_out) *dt_out = dt;
     free(u0); free(b0); free(rc); free(rb);

@@ -25,7 +25,7 @@ class Cfg(C.Structure):
                 ("gam", C.c_double), ("cfl", C.c_double),
                 ("uct", C.c_int), ("ho", C.c_int),
                 ("tol", C.c_double), ("maxit", C.c_int),
-                ("guess", C.c_int), ("nthreads", C.c_int)]
+                ("guess", C.c_int), ("nthreads", C.c_int), ("rec", C.c_int), ("rk", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -54,6 +54,8 @@ def lib():
         L.orc_hll.argtypes = [_dp, _dp, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp]
         L.orc_mp5.argtypes = [_dp]
         L.orc_mp5.restype = C.c_double
+        L.orc_mc.argtypes = [_dp]
+        L.orc_mc.restype = C.c_double
         L.orc_int.argtypes = [_dp, C.c_int]
         L.orc_int.restype = C.c_double
         L.orc_der.argtypes = [_dp, C.c_double, C.c_int]
@@ -129,6 +131,11 @@ def mp5(s):
     return lib().orc_mp5(_p(_vec(s)))
 
 
+def mc(s):
+    """Linear (MC-limited) value at i+1/2 from (u_{i-1}, u_i, u_{i+1})."""
+    return lib().orc_mc(_p(_vec(s)))
+
+
 def interp(s, ho):
     return lib().orc_int(_p(_vec(s)), int(ho))
 
@@ -179,9 +186,9 @@ class Grid:
     """Oracle state on a periodic nx*ny*nz grid: cons[5], face (or cell) B[3], W."""
 
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, gam=4.0 / 3.0, cfl=0.4,
-                 uct=1, ho=1, tol=1e-6, maxit=100, guess=GUESS_WARM, nthreads=0):
+                 uct=1, ho=1, tol=1e-6, maxit=100, guess=GUESS_WARM, nthreads=0, rec=0, rk=3):
         self.cfg = Cfg(nx, ny, nz, lx, ly, lz, gam, cfl, uct, ho, tol, maxit, guess,
-                       nthreads or int(os.environ.get("ORACLE_THREADS", "0")))
+                       nthreads or int(os.environ.get("ORACLE_THREADS", "0")), rec, rk)
         self.shape = (nz, ny, nx)
         self.n = nx * ny * nz
         self.cons = np.zeros((5,) + self.shape)

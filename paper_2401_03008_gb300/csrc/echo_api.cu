@@ -143,6 +143,7 @@ echo_status echo_config_default(echo_config *cfg)
     cfg->c2p_maxit = 100;
     cfg->device = 0;
     cfg->stream = nullptr;
+    cfg->rk_order = 3;
     return ECHO_OK;
 }
 
@@ -158,7 +159,10 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     if (!(cfg->cfl > 0.0)) return fail(nullptr, ECHO_ERR_ARG, "cfl must be > 0");
     if (cfg->uct != 0 && cfg->uct != 1) return fail(nullptr, ECHO_ERR_ARG, "uct must be 0 or 1");
     if (cfg->ho != 0 && cfg->ho != 1) return fail(nullptr, ECHO_ERR_ARG, "ho must be 0 or 1");
-    if (cfg->rec != ECHO_REC_MP5) return fail(nullptr, ECHO_ERR_ARG, "rec must be MP5");
+    if (cfg->rec != ECHO_REC_MP5 && cfg->rec != ECHO_REC_LINEAR)
+        return fail(nullptr, ECHO_ERR_ARG, "rec must be ECHO_REC_MP5 or ECHO_REC_LINEAR");
+    if (cfg->rk_order != 2 && cfg->rk_order != 3)
+        return fail(nullptr, ECHO_ERR_ARG, "rk_order must be 2 or 3");
     if (cfg->precision != ECHO_FP64 && cfg->precision != ECHO_MIXED)
         return fail(nullptr, ECHO_ERR_ARG, "precision must be FP64 or MIXED");
     if (cfg->c2p_guess < 0 || cfg->c2p_guess > 2)
@@ -191,6 +195,7 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     g.gfac = cfg->gamma_ad / (cfg->gamma_ad - 1.0);
     g.ho = cfg->ho;
     g.uct = cfg->uct;
+    g.rec = cfg->rec;
     c->mixed = cfg->precision == ECHO_MIXED;
     if (cudaSetDevice(cfg->device) != cudaSuccess) {
         delete c;
@@ -347,7 +352,7 @@ echo_status run_steps(echo_ctx *c, int max_steps, double t_end, int *steps_done,
     const bool finite_end = isfinite(t_end);
     for (int s = 0; s < max_steps; s++) {
         const long idx = step0 + s;
-        for (int stage = 1; stage <= 3; stage++) {
+        for (int stage = 1; stage <= c->cfg.rk_order; stage++) {
             if (c->mixed) launch_stage<float>(c, stage, idx, hv);
             else launch_stage<double>(c, stage, idx, hv);
         }

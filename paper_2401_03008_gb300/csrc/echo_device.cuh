@@ -22,6 +22,7 @@ struct Grid {
     double gfac;       // gam / (gam - 1)
     int ho;            // high-order INT / DER
     int uct;           // 1: staggered field + UCT; 0: cell-centred field, 8-component HLL
+    int rec;           // 0: MP5; 1: linear with the MC limiter
 };
 
 
@@ -230,6 +231,18 @@ struct Mp5Queue {
     }
     __device__ __forceinline__ R get(int k) const { return res[slot[k][threadIdx.x]]; }
 };
+
+// Linear reconstruction with the monotonized-central slope
+// minmod(2 (u_i - u_{i-1}), (u_{i+1} - u_{i-1})/2, 2 (u_{i+1} - u_i)): value at i+1/2
+template <typename R>
+__device__ __forceinline__ R mc_val(R um1, R u0, R up1)
+{
+    R a = R(2) * (u0 - um1), b = R(0.5) * (up1 - um1), c = R(2) * (up1 - u0);
+    R sl = R(0);
+    if (gtz(a) && gtz(b) && gtz(c)) sl = rmin(a, rmin(b, c));
+    else if (ltz(a) && ltz(b) && ltz(c)) sl = rmax(a, rmax(b, c));
+    return u0 + R(0.5) * sl;
+}
 
 // left state at i+1/2 from s[0..5] = u_{i-2..i+3}, and the mirrored right state
 template <typename R>

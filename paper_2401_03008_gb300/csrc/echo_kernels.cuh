@@ -163,10 +163,17 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
             // with UCT the normal field is the staggered face value, not reconstructed
             if (v == 5 + D && uct) continue;
             R s[6];
+            if (g.rec) {  // linear: cells i-1 .. i+2
 #pragma unroll
-            for (int m = 0; m < 6; m++) s[m] = ld(prim + v * n + cs[m]);
-            L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], 2 * v, mask);
-            Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], 2 * v + 1, mask);
+                for (int m = 1; m < 5; m++) s[m] = ld(prim + v * n + cs[m]);
+                L[v] = mc_val(s[1], s[2], s[3]);
+                Rt[v] = mc_val(s[4], s[3], s[2]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 6; m++) s[m] = ld(prim + v * n + cs[m]);
+                L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], 2 * v, mask);
+                Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], 2 * v + 1, mask);
+            }
         }
     }
     __syncthreads();
@@ -298,6 +305,17 @@ k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__re
     R r[12];
     unsigned mask = 0;
     long sb[6], sa[6];
+    const int lin = g.rec;
+    // left/right states of one stencil into slots k, k+1 of r
+    auto recon = [&](const R *s, int k) {
+        if (lin) {
+            r[k] = mc_val(s[1], s[2], s[3]);
+            r[k + 1] = mc_val(s[4], s[3], s[2]);
+        } else {
+            r[k] = q.defer(s[0], s[1], s[2], s[3], s[4], k, mask);
+            r[k + 1] = q.defer(s[5], s[4], s[3], s[2], s[1], k + 1, mask);
+        }
+    };
     if (active) {
         int i, j, k;
         coords(g, e, i, j, k);
@@ -311,21 +329,17 @@ k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__re
         for (int qs = 0; qs < 2; qs++) {
 #pragma unroll
             for (int m = 0; m < 6; m++) s[m] = ld(fda + (2 * qs) * n + sb[m]);
-            r[4 * qs + 0] = q.defer(s[0], s[1], s[2], s[3], s[4], 4 * qs + 0, mask);
-            r[4 * qs + 1] = q.defer(s[5], s[4], s[3], s[2], s[1], 4 * qs + 1, mask);
+            recon(s, 4 * qs + 0);
 #pragma unroll
             for (int m = 0; m < 6; m++) s[m] = ld(fda + (2 * qs + 1) * n + sb[m]);
-            r[4 * qs + 2] = q.defer(s[0], s[1], s[2], s[3], s[4], 4 * qs + 2, mask);
-            r[4 * qs + 3] = q.defer(s[5], s[4], s[3], s[2], s[1], 4 * qs + 3, mask);
+            recon(s, 4 * qs + 2);
         }
 #pragma unroll
         for (int m = 0; m < 6; m++) s[m] = ld(Bf + A * n + sb[m]);
-        r[8] = q.defer(s[0], s[1], s[2], s[3], s[4], 8, mask);
-        r[9] = q.defer(s[5], s[4], s[3], s[2], s[1], 9, mask);
+        recon(s, 8);
 #pragma unroll
         for (int m = 0; m < 6; m++) s[m] = ld(Bf + B * n + sa[m]);
-        r[10] = q.defer(s[0], s[1], s[2], s[3], s[4], 10, mask);
-        r[11] = q.defer(s[5], s[4], s[3], s[2], s[1], 11, mask);
+        recon(s, 10);
     }
     __syncthreads();
     q.process();
@@ -365,7 +379,7 @@ __device__ __forceinline__ R curl_a(const Grid &g, const R *__restrict__ E, int 
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(BS)
-k_rk(Grid g, int stage, const R *__restrict__ E, const R *__restrict__ rhs,
+k_rk(Grid g, int stage, int last, double a0, const R *__restrict__ E, const R *__restrict__ rhs,
      double *__restrict__ U, double *__restrict__ U0, double *__restrict__ Bf,
      double *__restrict__ Bf0, float *__restrict__ Bf32, DevScalars *sc)
 {
@@ -389,20 +403,20 @@ k_rk(Grid g, int stage, const R *__restrict__ E, const R *__restrict__ rhs,
                 pu0 = Bf0 + (v - 5) * n + c;
             }
             u = *pu;
+            // stage 1: U1 = Un + dt L; later stages: a0 Un + (1 - a0) (U + dt L)
+            // (SSP-RK3: a0 = 3/4, 1/3; SSP-RK2: a0 = 1/2)
             double un;
             if (stage == 1) {
                 *pu0 = u;
                 un = u + dt * r;
-            } else if (stage == 2) {
-                un = 0.75 * (*pu0) + 0.25 * (u + dt * r);
             } else {
-                un = (*pu0) * (1.0 / 3.0) + 2.0 / 3.0 * (u + dt * r);
+                un = (*pu0) * a0 + (1.0 - a0) * (u + dt * r);
             }
             *pu = un;
             if (v >= 5 && Bf32) Bf32[(v - 5) * n + c] = (float)un;
         }
     }
-    if (stage == 3 && blockIdx.x == 0 && threadIdx.x == 0) sc->step += 1;
+    if (last && blockIdx.x == 0 && threadIdx.x == 0) sc->step += 1;
 }
 
 // out (double) = sign * curl(E) on faces, accumulate or overwrite
@@ -494,7 +508,10 @@ void Path<R>::uct(echo_ctx *c)
 template <typename R>
 void Path<R>::rk(echo_ctx *c, int stage)
 {
-    launch(c, K_RK, k_rk<R>, nblocks(c->g.n, BS), BS, 0, c->g, stage, (const R *)c->E,
+    const int order = c->cfg.rk_order;
+    const double a0 = order == 2 ? 0.5 : (stage == 2 ? 0.75 : 1.0 / 3.0);
+    launch(c, K_RK, k_rk<R>, nblocks(c->g.n, BS), BS, 0, c->g, stage, stage == order ? 1 : 0, a0,
+           (const R *)c->E,
            (const R *)c->rhs, c->U, c->U0, c->Bf, c->Bf0, c->Bf32, c->sc);
 }
 

@@ -192,6 +192,7 @@ echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, i
     g.gfac = 0.0;
     g.ho = ho;
     g.uct = 1;
+    g.rec = 0;
     cudaStream_t s = (cudaStream_t)stream;
     const int nblk = (int)((n + NA_THREADS - 1) / NA_THREADS);
     k_na_partial<<<nblk, NA_THREADS, 0, s>>>(g, cons5, bface, scratch);

@@ -46,7 +46,7 @@ class Config(C.Structure):
                 ("uct", C.c_int), ("ho", C.c_int), ("rec", C.c_int),
                 ("precision", C.c_int), ("c2p_guess", C.c_int),
                 ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
-                ("device", C.c_int), ("stream", C.c_void_p)]
+                ("device", C.c_int), ("stream", C.c_void_p), ("rk_order", C.c_int)]
 
 
 class TrainCfg(C.Structure):
@@ -143,7 +143,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, L=(1.0, 1.0, 1.0), gamma=4.0 / 3.0, cfl=0.4, ho=1,
                  precision="fp64", guess="prev", tol=1e-6, maxit=100, device=0,
-                 stream=None, uct=1):
+                 stream=None, uct=1, rec="mp5", rk_order=3):
         self.L = lib()
         cfg = Config()
         self.L.echo_config_default(C.byref(cfg))
@@ -153,6 +153,8 @@ class Solver:
         cfg.cfl = cfl
         cfg.ho = ho
         cfg.uct = uct
+        cfg.rec = {"mp5": 0, "linear": 1}[rec]
+        cfg.rk_order = rk_order
         cfg.precision = {"fp64": FP64, "mixed": MIXED}[precision]
         cfg.c2p_guess = {"prev": GUESS_PREV, "cold": GUESS_COLD, "mlp": GUESS_MLP}[guess]
         cfg.c2p_tol = tol

@@ -34,13 +34,14 @@ def test_every_declared_symbol_is_exported():
 def test_config_default():
     cfg = echo.Config()
     assert echo.lib().echo_config_default(C.byref(cfg)) == echo.ECHO_OK
-    assert (cfg.nx, cfg.uct, cfg.ho, cfg.precision) == (32, 1, 1, echo.FP64)
+    assert (cfg.nx, cfg.uct, cfg.ho, cfg.precision, cfg.rk_order) == (32, 1, 1, echo.FP64, 3)
     assert cfg.gamma_ad == pytest.approx(4 / 3) and cfg.cfl == 0.4 and cfg.c2p_tol == 1e-6
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("lz", -1.0), ("gamma_ad", 1.0),
                                          ("cfl", 0.0), ("uct", 2), ("ho", 2), ("precision", 7),
-                                         ("c2p_guess", 5), ("c2p_maxit", 0)])
+                                         ("c2p_guess", 5), ("c2p_maxit", 0), ("rec", 2),
+                                         ("rk_order", 4)])
 def test_create_rejects_bad_config(field, value):
     L = echo.lib()
     cfg = echo.Config()

@@ -321,3 +321,20 @@ def test_cell_centred_turbulence_parity():
     g.step(4)
     s.step(4)
     assert_parity(s.primitives(), g.primitives(), PRIM_GROUPS, what="turbulence, uct off")
+
+
+@pytest.mark.parametrize("uct", [1, 0])
+def test_fast_variant_parity(uct):
+    """Linear reconstruction with SSP-RK2 (the faster variant of Sec. 4)."""
+    n = (24, 20, 16)
+    c = wl.CPA(*n, m=(1, 1, 1))
+    st = (c.prim5(), c.bcell(), None) if uct == 0 else (c.prim5(), c.bface_background(), c.apot())
+    ho = uct
+    g = orc.Grid(*n, uct=uct, ho=ho, rec=1, rk=2)
+    g.set_state(*st)
+    s = echo.Solver(*n, uct=uct, ho=ho, rec="linear", rk_order=2)
+    s.set_state(*st)
+    g.step(6)
+    done, t = s.step(6)
+    assert done == 6 and t == pytest.approx(g.t, rel=1e-13)
+    assert_parity(s.primitives(), g.primitives(), PRIM_GROUPS, what="linear + RK2")

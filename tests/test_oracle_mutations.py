@@ -63,6 +63,13 @@ MUTATIONS = [
     ("edge speeds taken at the wrong neighbour",
      "long ea1 = at(g, i, j, k, b, 1);", "long ea1 = at(g, i, j, k, a, 1);",
      [SC + "::test_brute_force_rhs"]),
+    ("mc slope limiter central term",
+     "b = 0.5 * (up1 - um1)", "b = 1.0 * (up1 - um1)",
+     [PW + "::test_linear_reconstruction_exact_on_lines_and_bounded"]),
+    ("rk2 final weight",
+     "cons[q] = 0.5 * u0[q] + 0.5 * (cons[q] + dt * rc[q]);",
+     "cons[q] = 0.4 * u0[q] + 0.6 * (cons[q] + dt * rc[q]);",
+     [SC + "::test_fast_variant_second_order"]),
     ("rk3 second-stage weight",
      "cons[q] = 0.75 * u0[q] + 0.25 * (cons[q] + dt * rc[q]);",
      "cons[q] = 0.7 * u0[q] + 0.3 * (cons[q] + dt * rc[q]);",

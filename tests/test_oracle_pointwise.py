@@ -403,3 +403,16 @@ def test_c2p_stopping_rule_reaches_rounding_floor():
     assert np.all(np.abs(W6 - W12) <= 16 * eps * np.maximum(u[4], W12))
     assert np.mean(np.abs(W6 - W12) / W12) < 1e-15
     assert np.mean(it6) < np.mean(it12)
+
+
+def test_linear_reconstruction_exact_on_lines_and_bounded():
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        a, b = rng.uniform(-1, 1, 2)
+        s = a + b * np.array([-1.0, 0.0, 1.0])
+        assert orc.mc(s) == pytest.approx(a + 0.5 * b, abs=1e-15)
+    # extrema and jumps: no new extremum (the value stays between u_i and u_{i+1})
+    for s in [(0, 1, 0), (1, 0, 1), (0, 0, 1), (0, 1, 1), (1, 1, 0)]:
+        v = orc.mc(s)
+        assert min(s[1], s[2]) - 1e-15 <= v <= max(s[1], s[2]) + 1e-15 or v == s[1]
+    assert orc.mc((0, 1, 0)) == 1.0

@@ -207,3 +207,26 @@ def test_cell_centred_variant_converges_and_conserves(ho):
     assert g.step(3) == 0
     scale = np.abs(g.cons).sum(axis=(1, 2, 3)).max()
     assert np.max(np.abs(g.totals() - t0)) <= 1e-13 * scale
+
+
+def test_fast_variant_second_order():
+    """Linear reconstruction with SSP-RK2 (the faster variant of Sec. 4): second
+    order on the wave, conservative."""
+    errs = []
+    for n in (32, 64, 128):
+        cpa = wl.CPA(n, 1, 1, m=(1, 0, 0))
+        g = orc.Grid(n, 1, 1, rec=1, rk=2)
+        g.set_state(cpa.prim5(), cpa.bface_background(), cpa.apot())
+        g.step(100000, t_end=0.25 * cpa.period)
+        p = g.primitives()
+        errs.append(np.max(np.mean(np.abs(p - cpa.exact_prim8(g.t)), axis=(1, 2, 3))[1:4]))
+    order = math.log2(errs[1] / errs[2])
+    assert 1.6 < order < 3.0, (errs, order)
+    g = orc.Grid(8, 6, 5, rec=1, rk=2)
+    prim, bg, apot = wl.random_smooth_fields(8, 6, 5, seed=25)
+    g.set_state(prim, bg, apot)
+    t0 = g.totals()
+    assert g.step(3) == 0
+    scale = np.abs(g.cons).sum(axis=(1, 2, 3)).max()
+    assert np.max(np.abs(g.totals() - t0)) <= 1e-13 * scale
+    assert np.max(np.abs(g.divb())) <= 1e-12 * np.abs(g.bf).max() * 8
