@@ -197,10 +197,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", type=int, default=1, help="also time mixed and mixed+learned")
-    ap.add_argument("--config", type=int, default=0, help="run benchmark-plan configuration 1..5")
+    ap.add_argument("--config", type=int, default=0,
+                    help="1..5: benchmark-plan configurations; 6: the 2.5-D turbulence run of Sec. 5")
     ap.add_argument("--config-steps", type=int, default=20)
     ap.add_argument("--config5-n", type=int, default=768)
     ap.add_argument("--config5-fp64-steps", type=int, default=5)
+    ap.add_argument("--config6-n", type=int, default=4096)
+    ap.add_argument("--config6-t", type=float, default=20.0)
+    ap.add_argument("--config6-out", default="", help="write the spectra (.npz) here")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -439,7 +443,9 @@ def run_config(args):
         return done, t, e0.elapsed_time(e1)
 
     out = {"config": args.config}
-    if args.config == 1:
+    if args.config == 6:
+        out.update(run_turbulence_2d(args, timed, sp))
+    elif args.config == 1:
         from oracle import oracle as orc
         n = 32
         c = wl.CPA(n, n, n, m=(1, 0, 0))
@@ -522,6 +528,77 @@ def run_config(args):
                                 "mean |dB|/B0 = 0.5, max Lorentz factor 2, |k| <= 4, seed %d"
                                 % (n, seed), "results": res})
     print(json.dumps(out))
+
+
+def run_turbulence_2d(args, timed, sp):
+    """Decaying 2.5-D Alfvenic turbulence (Sec. 5): n^2 x 1 cells of a (2 pi)^2 box,
+    sigma0 = 100, beta0 = 1, eta_rms = 0.25, modes |k| <= 4, UCT = HO = on, run to
+    t_end.  Every time unit: mean |dv_perp|/v_A, mean |dB_perp|/B0 and the rms of the
+    current J_z; at t = 0 and t_end the isotropised spectra of the perpendicular and
+    parallel components of v and B, with power-law slopes over ranges of k_perp."""
+    import numpy as np
+    import torch
+    from paper_2401_03008_gb300 import echo
+    from paper_2401_03008_gb300 import spectra
+    from paper_2401_03008_gb300 import workloads as wl
+    n, seed = args.config6_n, 2401_03008
+    tb = wl.Turbulence2D(n, seed=seed)
+    s = echo.Solver(n, n, 1, L=tb.L, precision=args.precision, guess=args.guess, ho=args.ho,
+                    uct=args.uct, rec=args.rec, rk_order=args.rk, stream=sp)
+    if args.uct:
+        s.set_state(tb.prim5(), tb.bface_background(), tb.apot())
+    else:
+        s.set_state(tb.prim5(), tb.bcell())
+    h = 2 * np.pi / n
+    prim = torch.empty((8, 1, n, n), dtype=torch.float64, device="cuda")
+
+    def sample(t):
+        s.primitives(prim)
+        v, B = prim[1:3, 0], prim[5:7, 0]
+        J = ((torch.roll(B[1], -1, 1) - torch.roll(B[1], 1, 1))
+             - (torch.roll(B[0], -1, 0) - torch.roll(B[0], 1, 0))) / (2 * h)
+        return {"t": t, "dv_over_vA": float(torch.sqrt((v * v).sum(0)).mean()) / tb.vA,
+                "dB_over_B0": float(torch.sqrt((B * B).sum(0)).mean()) / tb.B0,
+                "J_rms": float(torch.sqrt((J * J).mean()))}
+
+    def spec():
+        p = prim.cpu().numpy()[:, 0]
+        k, ev = spectra.shell_spectrum([p[1], p[2]])
+        _, eb = spectra.shell_spectrum([p[5], p[6]])
+        _, evz = spectra.shell_spectrum([p[3]])
+        _, ebz = spectra.shell_spectrum([p[7]])
+        return k, {"v_perp": ev, "B_perp": eb, "v_par": evz, "B_par": ebz}
+
+    series = [sample(0.0)]
+    k, spec0 = spec()
+    total_ms, steps, t, tk = 0.0, 0, 0.0, 0
+    while t < args.config6_t:
+        tk = min(tk + 1.0, args.config6_t)
+        done, t, ms = timed(s, 1 << 30, tk)
+        total_ms += ms
+        steps += done
+        series.append(sample(t))
+    k, spec1 = spec()
+    d = s.diagnostics()
+    ranges = [(8, 64), (16, 128), (32, 256), (64, 512)]
+    slopes = {name: {"%d-%d" % r: spectra.slope(k, e, *r) for r in ranges if r[1] <= n // 4}
+              for name, e in spec1.items()}
+    edges = np.unique(np.round(np.geomspace(1, n // 2, 40)).astype(int))
+    binned = {name: [float(e[lo:hi].mean()) for lo, hi in zip(edges[:-1], edges[1:])]
+              for name, e in spec1.items()}
+    if args.config6_out:
+        np.savez(args.config6_out, k=k, **{"t0_" + a: b for a, b in spec0.items()},
+                 **{"t1_" + a: b for a, b in spec1.items()})
+    return {"workload": "2.5-D decaying Alfvenic turbulence, %d^2 x 1, sigma0 = 100, beta0 = 1, "
+                        "eta_rms = 0.25, |k| <= 4, seed %d" % (n, seed),
+            "precision": args.precision, "uct": args.uct, "ho": args.ho, "rec": args.rec,
+            "rk_order": args.rk, "t_end": t, "steps": steps, "gpu_seconds": total_ms * 1e-3,
+            "gpu_seconds_per_time_unit": total_ms * 1e-3 / t,
+            "cell_updates_per_s": n * n * steps / (total_ms * 1e-3),
+            "divb_max": d["divb_max"], "newton_it_fp64": d["newton_it_mean"],
+            "c2p_fallbacks": d["c2p_fallbacks"], "c2p_failures": d["c2p_failures"],
+            "series": series, "slopes_t_end": slopes,
+            "spectra_t_end_binned": {"k_edges": edges.tolist(), **binned}}
 
 
 def end_to_end(args, s, n, world):

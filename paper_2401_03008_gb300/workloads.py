@@ -354,3 +354,91 @@ def mlp_init(seed):
         else:
             parts.append(np.zeros(int(np.prod(shape))))
     return np.concatenate(parts).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# 2.5-D decaying relativistic turbulence (the Sec. 5 run)
+# ---------------------------------------------------------------------------
+
+class Turbulence2D:
+    """The Sec. 5 set-up on an n x n x 1 grid of a (2 pi)^2 box: rho0 = 1, uniform B0
+    along z with sigma0 = B0^2/rho0 = 100 and beta0 = 2 p0/B0^2 = 1 (B0 = 10,
+    p0 = 50), fluid at rest, plus in-plane fluctuations
+      dv = eta_v sum_k (k/|k|) x e_z cos(k.x + phi_v(k)),
+      dB = eta_B sum_k (k/|k|) x e_z cos(k.x + phi_B(k)),
+    over kx = 0..4, ky = -4..4 with 1 <= |k| <= 4, independent random phases for v and
+    B (Sec. 5).  Both are divergence-free; dB enters as the curl of the edge potential
+    A_z = eta_B sum_k sin(k.x + phi_B)/|k|.  The amplitudes are fixed afterwards so
+    that the grid means of |dv|/v_A and |dB|/B0 equal eta_rms = 0.25, with
+    v_A = B0/sqrt(rho0 + 4 p0 + B0^2) (Sec. 5).  Seeded PCG64."""
+
+    def __init__(self, n, seed, sigma0=100.0, beta0=1.0, rho0=1.0, eta_rms=0.25, kmax=4,
+                 gam=GAMMA):
+        self.n = n
+        self.L = (2 * np.pi, 2 * np.pi, 2 * np.pi / n)
+        self.rho0, self.gam = rho0, gam
+        self.B0 = math.sqrt(sigma0 * rho0)
+        self.p0 = 0.5 * beta0 * self.B0 ** 2
+        self.vA = self.B0 / math.sqrt(rho0 + gam / (gam - 1.0) * self.p0 + self.B0 ** 2)
+        modes = [(kx, ky) for kx in range(0, kmax + 1) for ky in range(-kmax, kmax + 1)
+                 if 0 < kx * kx + ky * ky <= kmax * kmax]
+        self.modes = np.array(modes, dtype=np.float64)
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.phv = rng.uniform(0, 2 * np.pi, len(modes))
+        self.phB = rng.uniform(0, 2 * np.pi, len(modes))
+        self.kn = np.linalg.norm(self.modes, axis=1)
+        x = (np.arange(n) + 0.5) * 2 * np.pi / n
+        X, Y = np.meshgrid(x, x, indexing="xy")   # [y, x]
+        self._X, self._Y = X, Y
+        dv = self._field(self.phv, (0.5, 0.5))
+        dB = self._field(self.phB, (0.5, 0.5))
+        self.eta_v = eta_rms * self.vA / np.mean(np.sqrt(dv[0] ** 2 + dv[1] ** 2))
+        self.eta_B = eta_rms * self.B0 / np.mean(np.sqrt(dB[0] ** 2 + dB[1] ** 2))
+        self._dv = dv * self.eta_v
+
+    def _field(self, ph, off):
+        """unit-amplitude sum of (ky, -kx)/|k| cos(k.x + ph) at offset positions"""
+        h = 2 * np.pi / self.n
+        X = self._X + (off[0] - 0.5) * h
+        Y = self._Y + (off[1] - 0.5) * h
+        fx = np.zeros_like(X)
+        fy = np.zeros_like(X)
+        for q, (kx, ky) in enumerate(self.modes):
+            c = np.cos(kx * X + ky * Y + ph[q])
+            fx += ky / self.kn[q] * c
+            fy -= kx / self.kn[q] * c
+        return np.array([fx, fy])
+
+    def prim5(self):
+        n = self.n
+        out = np.zeros((5, 1, n, n))
+        out[0] = self.rho0
+        out[1, 0] = self._dv[0]
+        out[2, 0] = self._dv[1]
+        out[4] = self.p0
+        return out
+
+    def bface_background(self):
+        out = np.zeros((3, 1, self.n, self.n))
+        out[2] = self.B0
+        return out
+
+    def bcell(self):
+        """cell-centred B (the variant without UCT): B0 e_z plus the pointwise dB"""
+        out = np.zeros((3, 1, self.n, self.n))
+        dB = self._field(self.phB, (0.5, 0.5)) * self.eta_B
+        out[0, 0], out[1, 0], out[2] = dB[0], dB[1], self.B0
+        return out
+
+    def apot(self):
+        """A_z at the z-edges (i+1/2, j+1/2); A_x = A_y = 0."""
+        n = self.n
+        h = 2 * np.pi / n
+        X = self._X + 0.5 * h
+        Y = self._Y + 0.5 * h
+        az = np.zeros_like(X)
+        for q, (kx, ky) in enumerate(self.modes):
+            az += np.sin(kx * X + ky * Y + self.phB[q]) / self.kn[q]
+        out = np.zeros((3, 1, n, n))
+        out[2, 0] = self.eta_B * az
+        return out

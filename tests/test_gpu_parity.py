@@ -338,3 +338,27 @@ def test_fast_variant_parity(uct):
     done, t = s.step(6)
     assert done == 6 and t == pytest.approx(g.t, rel=1e-13)
     assert_parity(s.primitives(), g.primitives(), PRIM_GROUPS, what="linear + RK2")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_turbulence_2d_parity(precision):
+    """The 2.5-D set-up of Sec. 5 (nz = 1, sigma0 = 100) over one time unit on 80^2:
+    the z sweeps wrap onto the one layer and the z-edge field carries the in-plane
+    dynamics.  FP64 element by element; mixed within the FP32 reconstruction error."""
+    n = 80
+    tb = wl.Turbulence2D(n, seed=106)
+    st = (tb.prim5(), tb.bface_background(), tb.apot())
+    g = orc.Grid(n, n, 1, *tb.L, nthreads=8)
+    g.set_state(*st)
+    s = echo.Solver(n, n, 1, L=tb.L, precision=precision)
+    s.set_state(*st)
+    assert g.step(100000, t_end=1.0) == 0
+    done, t = s.step(100000, 1.0)
+    assert t == 1.0 and done == len(g.dts)
+    tol = FP64_TOL if precision == "fp64" else 1e-5
+    assert_parity(s.primitives(), g.primitives(), PRIM_GROUPS, tol=tol, what="2.5-D turbulence")
+    d = s.diagnostics()
+    # div B stays at the round-off of the precision the curl of E is taken in
+    b_over_h = tb.B0 * n / (2 * np.pi)
+    assert d["divb_max"] < (1e-11 if precision == "fp64" else 1e-7) * b_over_h
+    assert d["c2p_failures"] == 0
