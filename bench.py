@@ -198,7 +198,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", type=int, default=1, help="also time mixed and mixed+learned")
     ap.add_argument("--config", type=int, default=0,
-                    help="1..5: benchmark-plan configurations; 6: the 2.5-D turbulence run of Sec. 5")
+                    help="1..5: benchmark-plan configurations; 6: the 2.5-D turbulence run of "
+                         "Sec. 5; 7: 2 x 2 x 2 blocks with the wide halo against one grid")
     ap.add_argument("--config-steps", type=int, default=20)
     ap.add_argument("--config5-n", type=int, default=768)
     ap.add_argument("--config5-fp64-steps", type=int, default=5)
@@ -445,6 +446,8 @@ def run_config(args):
     out = {"config": args.config}
     if args.config == 6:
         out.update(run_turbulence_2d(args, timed, sp))
+    elif args.config == 7:
+        out.update(run_blocks(args, timed, sp))
     elif args.config == 1:
         from oracle import oracle as orc
         n = 32
@@ -599,6 +602,39 @@ def run_turbulence_2d(args, timed, sp):
             "c2p_fallbacks": d["c2p_fallbacks"], "c2p_failures": d["c2p_failures"],
             "series": series, "slopes_t_end": slopes,
             "spectra_t_end_binned": {"k_edges": edges.tolist(), **binned}}
+
+
+def run_blocks(args, timed, sp):
+    """The grid split into 2 x 2 x 2 blocks with the wide halo (one exchange per
+    substep), all on this GPU, against the undecomposed grid: rate and identity of
+    the state after the same steps."""
+    import numpy as np
+    from paper_2401_03008_gb300 import echo
+    n = args.n
+    _, st = workload_state(n, args.wave)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        kw = dict(precision=prec, stream=sp)
+        s = echo.Solver(n, n, n, **kw)
+        s.set_state(*st)
+        s.step(1)
+        _, _, ms_s = timed(s, args.config_steps)
+        d = echo.Decomp(n, n, n, (2, 2, 2), **kw)
+        d.set_state(*st)
+        d.step(1)
+        _, _, ms_d = timed(d, args.config_steps)
+        a, b = s.get_state(), d.get_state()
+        same = all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])) and a[3:] == b[3:]
+        npad = (n // 2 + 2 * d.halo)
+        res[prec] = {"halo": d.halo, "padded_block": npad,
+                     "padded_volume_ratio": 8 * npad ** 3 / n ** 3,
+                     "single_grid_cell_updates_per_s": n ** 3 * args.config_steps / (ms_s * 1e-3),
+                     "blocks_cell_updates_per_s": n ** 3 * args.config_steps / (ms_d * 1e-3),
+                     "state_bit_identical": bool(same)}
+        s.close()
+        d.close()
+    return {"workload": "Alfven wave along (1,1,1), %d^3, 2 x 2 x 2 blocks with the minimum "
+                        "wide halo, %d steps" % (n, args.config_steps), "results": res}
 
 
 def end_to_end(args, s, n, world):

@@ -262,6 +262,66 @@ echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, i
                                      int ny, int nz, double lx, double ly, double lz, int ho,
                                      void *stream, double *out, int out_kind);
 
+/* ---------------------------------------------------------------------------
+ * Block domain decomposition with a wide halo, all subdomains on one device.
+ *
+ * Sec. 3 splits the periodic grid into blocks, one MPI rank each, and fills ghost
+ * cells before every loop that calls INT, REC or DER; Sec. 4 and Sec. 6 propose
+ * instead a halo wide enough that one exchange per Runge-Kutta substep, of all
+ * variables at once, serves the whole substep.  This object is that plan with the
+ * ranks kept on one GPU: the grid of cfg is split into px * py * pz equal blocks,
+ * each stored as a padded block with `halo` ghost cells on both sides of every
+ * split direction (none along an unsplit one, which stays periodic on itself).
+ * Before each substep one exchange copies, for every ghost cell of every block, U
+ * (5), the face field (3) and the Newton guess W from the block that owns the
+ * cell; each block then runs the single-grid substep kernels on its padded
+ * extent, and only its owned cells are kept.  The step's speed
+ * maximum is taken over the owned faces of all blocks (the allreduce(max) of a
+ * multi-rank run), so every block takes the same dt.  With halo >=
+ * echo_decomp_min_halo(cfg) the owned cells come out bit-identical to those of one
+ * undecomposed context with the same cfg; a narrower halo lets the blocks' seams
+ * reach them.  The blocks share one stream (cfg->stream, or one the object
+ * creates); the learned guess is not available here (ECHO_ERR_ARG). */
+typedef struct echo_decomp echo_decomp;
+
+/* The dependency radius, in cells, of one substep on the exchanged data: the DER
+ * stencil (3 faces with HO, 1 without), the REC stencil (2 cells for MP5, 1 for
+ * linear) and the INT stencil (2 faces with HO, 1 without, 0 without UCT), summed
+ * over the upwind side.  Returns -1 for a NULL or invalid cfg. */
+int echo_decomp_min_halo(const echo_config *cfg);
+
+/* cfg: the global grid and scheme, as for echo_create.  px, py, pz >= 1 blocks per
+ * direction, each dividing the cells of its direction; halo >= 1 ghost cells.
+ * Errors: ECHO_ERR_ARG, ECHO_ERR_OOM, ECHO_ERR_CUDA (text in
+ * echo_decomp_last_error(NULL)). */
+echo_status echo_decomp_create(const echo_config *cfg, int px, int py, int pz, int halo,
+                               echo_decomp **out);
+echo_status echo_decomp_destroy(echo_decomp *d);
+
+/* Global arrays in the layouts of echo_set_state, host or device (ptr_kind). */
+echo_status echo_decomp_set_state(echo_decomp *d, const double *prim, const double *bface,
+                                  const double *apot, int ptr_kind);
+
+/* As echo_step, on all blocks; on ECHO_ERR_C2P every block returns to the start of
+ * the failed step. */
+echo_status echo_decomp_step(echo_decomp *d, int max_steps, double t_end, int *steps_done,
+                             double *t_now);
+
+/* Global outputs assembled from the owned cells, in the layouts of echo_get_state
+ * and echo_get_primitives (any of cons5, bface, w, t, step may be NULL). */
+echo_status echo_decomp_get_state(echo_decomp *d, double *cons5, double *bface, double *w,
+                                  double *t, long *step, int ptr_kind);
+echo_status echo_decomp_get_primitives(echo_decomp *d, double *out, int ptr_kind);
+
+/* Inversion statistics of the owned cells of all blocks since set_state:
+ * out[0] = inversions, out[1] = FP64 Newton iterations summed, out[2] = largest
+ * iteration count, out[3] = failed inversions, out[4] = interface states reset
+ * to first order. */
+echo_status echo_decomp_counters(echo_decomp *d, double *out);
+
+/* Text of the last error on d (a static string when d is NULL). */
+const char *echo_decomp_last_error(const echo_decomp *d);
+
 /* The context's stream (cudaStream_t) and device. */
 void *echo_stream(const echo_ctx *ctx);
 

@@ -196,6 +196,11 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     g.ho = cfg->ho;
     g.uct = cfg->uct;
     g.rec = cfg->rec;
+    g.lo[0] = g.lo[1] = g.lo[2] = 0;
+    g.hi[0] = g.nx;
+    g.hi[1] = g.ny;
+    g.hi[2] = g.nz;
+    g.primary = 1;
     c->mixed = cfg->precision == ECHO_MIXED;
     if (cudaSetDevice(cfg->device) != cudaSuccess) {
         delete c;

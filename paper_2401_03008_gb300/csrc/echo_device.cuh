@@ -23,7 +23,18 @@ struct Grid {
     int ho;            // high-order INT / DER
     int uct;           // 1: staggered field + UCT; 0: cell-centred field, 8-component HLL
     int rec;           // 0: MP5; 1: linear with the MC limiter
+    // Owned box [lo, hi) per direction: the cells whose inversion statistics and
+    // right-face speeds count (the whole grid, except for a padded subdomain, whose
+    // ghost cells are updated too but belong to a neighbour).
+    int lo[3], hi[3];
+    int primary;       // 1: this grid advances the step counter
 };
+
+__device__ __forceinline__ bool owned(const Grid &g, int i, int j, int k)
+{
+    return i >= g.lo[0] && i < g.hi[0] && j >= g.lo[1] && j < g.hi[1] && k >= g.lo[2] &&
+           k < g.hi[2];
+}
 
 
 // Device-side scalars of the time loop and the health counters.

@@ -39,10 +39,11 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
     const long n = g.n;
     long c = blockIdx.x * (long)BS + threadIdx.x;
     unsigned it = 0, it32 = 0;
-    bool active = c < n, bad = false, fb = false;
+    bool active = c < n, bad = false, fb = false, own = false;
     if (active) {
         int i, j, k;
         coords(g, c, i, j, k);
+        own = owned(g, i, j, k);
         double B[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) B[d] = cell_field(g, Bf, c, i, j, k, d);
@@ -77,12 +78,16 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
 #pragma unroll
         for (int v = 0; v < 3; v++) prim[(5 + v) * n + c] = (R)B[v];
         if (update_w) W[c] = Wn;
+        if (!own) {  // a neighbour's cell: updated, not counted
+            it = it32 = 0;
+            bad = fb = false;
+        }
     }
     if (!count) return;
     unsigned s = __reduce_add_sync(0xffffffffu, it);
     unsigned s32 = __reduce_add_sync(0xffffffffu, it32);
     unsigned m = __reduce_max_sync(0xffffffffu, it);
-    unsigned na = __popc(__ballot_sync(0xffffffffu, active));
+    unsigned na = __popc(__ballot_sync(0xffffffffu, own));
     unsigned nb = __popc(__ballot_sync(0xffffffffu, bad));
     unsigned nf = __popc(__ballot_sync(0xffffffffu, fb));
     if ((threadIdx.x & 31) == 0) {
@@ -153,9 +158,11 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
     long cs[6];
     R L[8], Rt[8];
     unsigned mask = 0;
+    bool own = false;  // face i+1/2 belongs to cell i
     if (active) {
         int i, j, k;
         coords(g, f, i, j, k);
+        own = owned(g, i, j, k);
 #pragma unroll
         for (int m = 0; m < 6; m++) cs[m] = shifted<D>(g, i, j, k, m - 2);
 #pragma unroll
@@ -208,7 +215,7 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
                 nfb++;
             }
         }
-        if (nfb) atomicAdd(&sc->rec_fallbacks, (unsigned)nfb);
+        if (nfb && own) atomicAdd(&sc->rec_fallbacks, (unsigned)nfb);
         const R gam = (R)g.gam;
         const R gfac = (R)g.gfac;
         R UL[8], FL[8], UR[8], FR[8], lmL, lpL, lmR, lpR;
@@ -238,7 +245,7 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
             fd[4 * n + f] = ap;
             fd[5 * n + f] = am;
         }
-        amax = rmax(ap, am);
+        if (own) amax = rmax(ap, am);
     }
     if (want_amax) {
         // block maximum in R (non-negative values), one conversion per block
@@ -416,7 +423,7 @@ k_rk(Grid g, int stage, int last, double a0, const R *__restrict__ E, const R *_
             if (v >= 5 && Bf32) Bf32[(v - 5) * n + c] = (float)un;
         }
     }
-    if (last && blockIdx.x == 0 && threadIdx.x == 0) sc->step += 1;
+    if (last && g.primary && blockIdx.x == 0 && threadIdx.x == 0) sc->step += 1;
 }
 
 // out (double) = sign * curl(E) on faces, accumulate or overwrite

@@ -193,6 +193,11 @@ echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, i
     g.ho = ho;
     g.uct = 1;
     g.rec = 0;
+    g.lo[0] = g.lo[1] = g.lo[2] = 0;
+    g.hi[0] = nx;
+    g.hi[1] = ny;
+    g.hi[2] = nz;
+    g.primary = 1;
     cudaStream_t s = (cudaStream_t)stream;
     const int nblk = (int)((n + NA_THREADS - 1) / NA_THREADS);
     k_na_partial<<<nblk, NA_THREADS, 0, s>>>(g, cons5, bface, scratch);

@@ -29,7 +29,10 @@ EXPORTS = ["echo_config_default", "echo_create", "echo_destroy", "echo_set_state
            "echo_set_conserved", "echo_diagnostics", "echo_l1_error", "echo_profile_enable",
            "echo_profile_read", "echo_launches", "echo_probe_fma_peak", "echo_stream",
            "echo_last_error", "echo_diagnostics_noalloc", "echo_mlp_load", "echo_mlp_forward",
-           "echo_mlp_grad", "echo_mlp_train", "echo_mlp_harvest"]
+           "echo_mlp_grad", "echo_mlp_train", "echo_mlp_harvest", "echo_decomp_min_halo",
+           "echo_decomp_create", "echo_decomp_destroy", "echo_decomp_set_state",
+           "echo_decomp_step", "echo_decomp_get_state", "echo_decomp_get_primitives",
+           "echo_decomp_counters", "echo_decomp_last_error"]
 MLP_NPARAM = 4609
 
 
@@ -112,6 +115,16 @@ def lib():
     L.echo_mlp_grad.argtypes = [fp, vp, vp, C.c_long, fp, fp, vp]
     L.echo_mlp_train.argtypes = [vp, vp, C.c_long, C.POINTER(TrainCfg), fp, fp, vp]
     L.echo_mlp_harvest.argtypes = [vp, ip, C.c_long, vp, vp, C.c_long, C.POINTER(C.c_long)]
+    L.echo_decomp_min_halo.argtypes = [C.POINTER(Config)]
+    L.echo_decomp_create.argtypes = [C.POINTER(Config), ip, ip, ip, ip, C.POINTER(vp)]
+    L.echo_decomp_destroy.argtypes = [vp]
+    L.echo_decomp_set_state.argtypes = [vp, vp, vp, vp, ip]
+    L.echo_decomp_step.argtypes = [vp, ip, C.c_double, C.POINTER(C.c_int), dp]
+    L.echo_decomp_get_state.argtypes = [vp, vp, vp, vp, dp, C.POINTER(C.c_long), ip]
+    L.echo_decomp_get_primitives.argtypes = [vp, vp, ip]
+    L.echo_decomp_counters.argtypes = [vp, dp]
+    L.echo_decomp_last_error.argtypes = [vp]
+    L.echo_decomp_last_error.restype = C.c_char_p
     _lib = L
     return L
 
@@ -138,29 +151,35 @@ def _ptr(x, what, count):
     return C.c_void_p(x.ctypes.data), PTR_HOST
 
 
+def make_config(nx, ny, nz, L=(1.0, 1.0, 1.0), gamma=4.0 / 3.0, cfl=0.4, ho=1,
+                precision="fp64", guess="prev", tol=1e-6, maxit=100, device=0, stream=None,
+                uct=1, rec="mp5", rk_order=3):
+    """echo_config from keyword arguments (the defaults of echo_config_default)."""
+    cfg = Config()
+    lib().echo_config_default(C.byref(cfg))
+    cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+    cfg.lx, cfg.ly, cfg.lz = L
+    cfg.gamma_ad = gamma
+    cfg.cfl = cfl
+    cfg.ho = ho
+    cfg.uct = uct
+    cfg.rec = {"mp5": 0, "linear": 1}[rec]
+    cfg.rk_order = rk_order
+    cfg.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    cfg.c2p_guess = {"prev": GUESS_PREV, "cold": GUESS_COLD, "mlp": GUESS_MLP}[guess]
+    cfg.c2p_tol = tol
+    cfg.c2p_maxit = maxit
+    cfg.device = device
+    cfg.stream = stream
+    return cfg
+
+
 class Solver:
     """One libecho context: a periodic grid with its state on the GPU."""
 
-    def __init__(self, nx, ny, nz, L=(1.0, 1.0, 1.0), gamma=4.0 / 3.0, cfl=0.4, ho=1,
-                 precision="fp64", guess="prev", tol=1e-6, maxit=100, device=0,
-                 stream=None, uct=1, rec="mp5", rk_order=3):
+    def __init__(self, nx, ny, nz, L=(1.0, 1.0, 1.0), **kw):
         self.L = lib()
-        cfg = Config()
-        self.L.echo_config_default(C.byref(cfg))
-        cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
-        cfg.lx, cfg.ly, cfg.lz = L
-        cfg.gamma_ad = gamma
-        cfg.cfl = cfl
-        cfg.ho = ho
-        cfg.uct = uct
-        cfg.rec = {"mp5": 0, "linear": 1}[rec]
-        cfg.rk_order = rk_order
-        cfg.precision = {"fp64": FP64, "mixed": MIXED}[precision]
-        cfg.c2p_guess = {"prev": GUESS_PREV, "cold": GUESS_COLD, "mlp": GUESS_MLP}[guess]
-        cfg.c2p_tol = tol
-        cfg.c2p_maxit = maxit
-        cfg.device = device
-        cfg.stream = stream
+        cfg = make_config(nx, ny, nz, L, **kw)
         self.cfg = cfg
         self.shape = (nz, ny, nx)
         self.n = nx * ny * nz
@@ -308,6 +327,79 @@ class Solver:
     @property
     def stream(self):
         return self.L.echo_stream(self._h)
+
+
+class Decomp:
+    """The grid split into px * py * pz blocks with a wide halo, all on one GPU
+    (echo_decomp_*): one exchange of every variable per Runge-Kutta substep."""
+
+    def __init__(self, nx, ny, nz, blocks, halo=None, L=(1.0, 1.0, 1.0), **kw):
+        self.L = lib()
+        self.cfg = make_config(nx, ny, nz, L, **kw)
+        self.min_halo = self.L.echo_decomp_min_halo(C.byref(self.cfg))
+        self.halo = self.min_halo if halo is None else halo
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        self._h = C.c_void_p()
+        self._check(self.L.echo_decomp_create(C.byref(self.cfg), *blocks, self.halo,
+                                              C.byref(self._h)), None)
+
+    def _check(self, st, h="self"):
+        if st != ECHO_OK:
+            handle = self._h if h == "self" else None
+            raise EchoError(st, self.L.echo_decomp_last_error(handle).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.echo_decomp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, prim, bface=None, apot=None):
+        n = self.n
+        p, kp = _ptr(prim, "prim", 5 * n)
+        b, kb = _ptr(bface, "bface", 3 * n)
+        a, ka = _ptr(apot, "apot", 3 * n)
+        kind = Solver._same_kind(kp, kb, ka)
+        Solver._sync_torch(kind)
+        self._check(self.L.echo_decomp_set_state(self._h, p, b, a, kind))
+
+    def step(self, max_steps=1, t_end=math.inf):
+        done = C.c_int()
+        t = C.c_double()
+        self._check(self.L.echo_decomp_step(self._h, max_steps, t_end, C.byref(done),
+                                            C.byref(t)))
+        return done.value, t.value
+
+    def primitives(self):
+        out = np.empty((8,) + self.shape)
+        p, kind = _ptr(out, "out", 8 * self.n)
+        self._check(self.L.echo_decomp_get_primitives(self._h, p, kind))
+        return out
+
+    def get_state(self):
+        n = self.n
+        cons = np.empty((5,) + self.shape)
+        bface = np.empty((3,) + self.shape)
+        w = np.empty(self.shape)
+        t = C.c_double()
+        step = C.c_long()
+        self._check(self.L.echo_decomp_get_state(
+            self._h, _ptr(cons, "cons", 5 * n)[0], _ptr(bface, "bface", 3 * n)[0],
+            _ptr(w, "w", n)[0], C.byref(t), C.byref(step), PTR_HOST))
+        return cons, bface, w, t.value, step.value
+
+    def counters(self):
+        out = (C.c_double * 5)()
+        self._check(self.L.echo_decomp_counters(self._h, out))
+        return {"c2p_calls": int(out[0]), "newton_it_sum": int(out[1]),
+                "newton_it_max": int(out[2]), "c2p_failures": int(out[3]),
+                "rec_fallbacks": int(out[4])}
 
 
 # ---------------------------------------------------------------------------

@@ -73,3 +73,29 @@ def test_create_without_gpu_reports_cuda_error():
     assert L.echo_create(C.byref(cfg), C.byref(h)) == echo.ECHO_ERR_CUDA
     with pytest.raises(echo.EchoError):
         echo.Solver(8, 8, 8)
+
+
+@pytest.mark.parametrize("uct,ho,rec,expect", [(1, 1, 0, 7), (1, 0, 0, 4), (0, 1, 0, 5),
+                                                (0, 0, 0, 3), (1, 1, 1, 6), (0, 0, 1, 2)])
+def test_decomp_min_halo(uct, ho, rec, expect):
+    """The upwind dependency radius of one substep: DER faces (3 with HO, else 1)
+    + REC cells (2 for MP5, 1 linear) + INT faces (2 with HO, 1 without, 0 when
+    the field is cell-centred)."""
+    cfg = echo.make_config(8, 8, 8, uct=uct, ho=ho, rec=["mp5", "linear"][rec])
+    assert echo.lib().echo_decomp_min_halo(C.byref(cfg)) == expect
+    cfg.ho = 3
+    assert echo.lib().echo_decomp_min_halo(C.byref(cfg)) == -1
+    assert echo.lib().echo_decomp_min_halo(None) == -1
+
+
+@pytest.mark.parametrize("blocks,halo,guess", [((3, 1, 1), 7, "prev"), ((2, 0, 1), 7, "prev"),
+                                               ((2, 2, 2), 0, "prev"), ((2, 1, 1), 7, "mlp")])
+def test_decomp_rejects_bad_arguments(blocks, halo, guess):
+    L = echo.lib()
+    cfg = echo.make_config(16, 8, 8, guess=guess)
+    h = C.c_void_p()
+    assert L.echo_decomp_create(C.byref(cfg), *blocks, halo, C.byref(h)) == echo.ECHO_ERR_ARG
+    assert not h.value and L.echo_decomp_last_error(None)
+    assert L.echo_decomp_create(None, 1, 1, 1, 1, C.byref(h)) == echo.ECHO_ERR_ARG
+    assert L.echo_decomp_step(None, 1, 1.0, None, None) == echo.ECHO_ERR_ARG
+    assert L.echo_decomp_destroy(None) == echo.ECHO_OK
