@@ -69,10 +69,13 @@ def test_block_shapes(blocks):
 @pytest.mark.parametrize("kw", [dict(), dict(uct=0, ho=0)], ids=["uct-ho-mp5", "uct0-ho0"])
 def test_narrower_halo_differs(kw):
     """One ghost layer less than the radius: the seam's garbage reaches the first
-    owned cells within one substep."""
-    s, d, r1, r2 = _pair((2, 1, 1), halo_delta=-1, steps=1, **kw)
+    owned cells within one substep.  Three blocks of 8 along x: a padded block of
+    exactly N cells (two blocks of 12 with a halo of 6) would be a whole periodic
+    copy of the line and hold no garbage at all."""
+    s, d, r1, r2 = _pair((3, 1, 1), halo_delta=-1, steps=1, **kw)
+    assert 8 + 2 * d.halo != N[0]
     assert not _same(s, d)
-    s2, d2, _, _ = _pair((2, 1, 1), halo_delta=+2, steps=1, **kw)
+    s2, d2, _, _ = _pair((3, 1, 1), halo_delta=+2, steps=1, **kw)
     assert _same(s2, d2)
 
 
