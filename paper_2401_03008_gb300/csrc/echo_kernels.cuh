@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(MLP_BS)
 k_mlp_guess(Grid g, const double *__restrict__ U, const BT *__restrict__ Bf,
             const MlpDev *__restrict__ w, float *__restrict__ guess)
 {
-    __shared__ __align__(16) MlpDev sw;
-    load_mlp_shared(sw, w);
+    __shared__ __align__(16) unsigned char smem[MLP_INFER_BYTES];
+    const MlpDev &sw = load_mlp_shared(smem, w);
     const int lane = threadIdx.x & 31;
     const long n = g.n;
     for (long base = blockIdx.x * (long)MLP_BS; base < n; base += (long)gridDim.x * MLP_BS) {

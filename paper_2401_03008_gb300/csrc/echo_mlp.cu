@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(MLP_BS)
 k_mlp_forward(long n, const float *__restrict__ feats, const MlpDev *__restrict__ w,
               float *__restrict__ y)
 {
-    __shared__ __align__(16) MlpDev sw;
-    load_mlp_shared(sw, w);
+    __shared__ __align__(16) unsigned char smem[MLP_INFER_BYTES];
+    const MlpDev &sw = load_mlp_shared(smem, w);
     const long s = blockIdx.x * (long)MLP_BS + threadIdx.x;
     float x[NIN] = {0.5f, 0.f, 0.f, 0.f, 1.f};
     if (s < n)
@@ -46,6 +46,11 @@ __global__ void k_mlp_build(const float *__restrict__ p, MlpDev *w)
         int o = q / NH, i = q % NH;
         w->W2[q] = __float2bfloat16_rn(p[O_W2 + q]);
         w->W2T[i * NH + o] = __float2bfloat16_rn(p[O_W2 + q]);
+    }
+    for (int q = threadIdx.x; q < (NH / 8) * (NH / 16) * 32; q += blockDim.x) {
+        const int nt = q / 128, kk = (q / 32) % 4, lane = q % 32, g = lane >> 2, t = lane & 3;
+        const float *row = p + O_W2 + (8 * nt + g) * NH + 16 * kk + 2 * t;
+        w->W2F[nt][kk][lane] = make_uint2(pack_bf16(row[0], row[1]), pack_bf16(row[8], row[9]));
     }
     for (int q = threadIdx.x; q < NH * NIN; q += blockDim.x) w->W1[q] = p[O_W1 + q];
     for (int q = threadIdx.x; q < NH; q += blockDim.x) {

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <stddef.h>
 
 #include "echo_device.cuh"
 
@@ -19,7 +20,8 @@ constexpr int NPARAM = NH * NIN + NH + NH * NH + NH + NH + 1;  // 4609
 constexpr int O_W1 = 0, O_B1 = O_W1 + NH * NIN, O_W2 = O_B1 + NH, O_B2 = O_W2 + NH * NH,
               O_W3 = O_B2 + NH, O_B3 = O_W3 + NH;
 
-// device form of the parameters used by the kernels
+// device form of the parameters used by the kernels.  The inference kernels copy
+// the prefix up to W2 (MLP_INFER_BYTES) to shared memory; W2 and W2T serve training.
 struct MlpDev {
     float W1[NH * NIN];
     float b1[NH];
@@ -27,9 +29,18 @@ struct MlpDev {
     float w3[NH];
     float b3;
     float pad[3];
+    // B fragments of the hidden-layer product, [n-tile][k-tile][lane]: for lane
+    // 4 g + t, (W2[8 nt + g][16 kk + 2t .. +1], W2[8 nt + g][16 kk + 2t + 8 .. +9])
+    // as bf16 pairs, so that a warp reads one n-tile / k-tile in one 8-byte load
+    uint2 W2F[NH / 8][NH / 16][32];
     __nv_bfloat16 W2[NH * NH];   // [out][in]
     __nv_bfloat16 W2T[NH * NH];  // [in][out]
 };
+constexpr int MLP_INFER_BYTES = (int)offsetof(MlpDev, W2);
+static_assert(MLP_INFER_BYTES % 16 == 0, "inference prefix is copied in 16-byte words");
+static_assert(offsetof(MlpDev, b1) % 8 == 0 && offsetof(MlpDev, b2) % 8 == 0 &&
+                  offsetof(MlpDev, w3) % 8 == 0 && offsetof(MlpDev, W2F) % 8 == 0,
+              "pairs are read as float2 / uint2");
 
 __device__ __forceinline__ void mma_bf16(float *c, const unsigned *a, unsigned b0, unsigned b1)
 {
@@ -73,99 +84,105 @@ __device__ __forceinline__ void mlp_features(const double *u, const double *B, f
 }
 
 // Forward pass of the 32 samples of a warp (lane = sample; x of inactive lanes is
-// ignored).  Returns y of the lane's own sample.  Layout of the m16n8k16
-// fragments: lane = 4 g + t; A rows g, g+8, cols 2t(+1), 2t+8(+1); B col g,
-// rows 2t(+1), 2t+8(+1); C rows g, g+8, cols 2t, 2t+1.  The tanh outputs of the
-// first layer land in exactly the A layout of the second product.
+// ignored).  Returns y of the lane's own sample.  The warp's 32 samples form two
+// m-tiles of the m16n8k16 product; lane 4 g + t holds rows g and g + 8 of both,
+// that is samples g, g + 8, g + 16, g + 24.  Fragment layouts: A rows g, g+8,
+// cols 2t(+1), 2t+8(+1); B col g, rows 2t(+1), 2t+8(+1); C rows g, g+8, cols 2t,
+// 2t+1.  The first layer computes exactly the hidden values of the lane's A
+// fragments; each B fragment of W2 is read once and serves both m-tiles; the
+// second layer's tanh and the output dot product run on the C fragments of one
+// n-tile at a time, so only the A fragments stay live across the product.
 __device__ __forceinline__ float mlp_warp_forward(const MlpDev &w, const float *x, int lane)
 {
     const unsigned FULL = 0xffffffffu;
     const int g = lane >> 2, t = lane & 3;
-    float ysel[2][2];
-    // not unrolled: keeps the compiler from holding the first-layer weights of both
-    // m-tiles in registers at once
-#pragma unroll 1
-    for (int mt = 0; mt < 2; mt++) {
-        float xa[NIN], xb[NIN];
+    unsigned A[2][4][4];
+    {
+        float xs[4][NIN];
 #pragma unroll
-        for (int f = 0; f < NIN; f++) {
-            xa[f] = __shfl_sync(FULL, x[f], 16 * mt + g);
-            xb[f] = __shfl_sync(FULL, x[f], 16 * mt + g + 8);
-        }
-        unsigned A[4][4];
+        for (int r = 0; r < 4; r++)
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            float ha[2], hb[2];
+            for (int f = 0; f < NIN; f++) xs[r][f] = __shfl_sync(FULL, x[f], g + 8 * r);
 #pragma unroll
-            for (int e = 0; e < 2; e++) {
-                const int col = 8 * j + 2 * t + e;
-                float za = w.b1[col], zb = w.b1[col];
+        for (int j = 0; j < 8; j++) {  // hidden columns 8 j + 2 t, 8 j + 2 t + 1
+            const int col = 8 * j + 2 * t;
+            const float2 bb = *reinterpret_cast<const float2 *>(&w.b1[col]);
+            float wv[2 * NIN];  // rows col and col + 1 of W1: ten consecutive floats
+            const float2 *wp = reinterpret_cast<const float2 *>(&w.W1[col * NIN]);
+#pragma unroll
+            for (int q = 0; q < NIN; q++) {
+                const float2 v = wp[q];
+                wv[2 * q] = v.x;
+                wv[2 * q + 1] = v.y;
+            }
+            float h[4][2];
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                float za = bb.x, zb = bb.y;
 #pragma unroll
                 for (int f = 0; f < NIN; f++) {
-                    za = fmaf(w.W1[col * NIN + f], xa[f], za);
-                    zb = fmaf(w.W1[col * NIN + f], xb[f], zb);
+                    za = fmaf(wv[f], xs[r][f], za);
+                    zb = fmaf(wv[NIN + f], xs[r][f], zb);
                 }
-                ha[e] = tanh_fast(za);
-                hb[e] = tanh_fast(zb);
+                h[r][0] = tanh_fast(za);
+                h[r][1] = tanh_fast(zb);
             }
             const int kk = j >> 1, hi = j & 1;
-            A[kk][2 * hi + 0] = pack_bf16(ha[0], ha[1]);
-            A[kk][2 * hi + 1] = pack_bf16(hb[0], hb[1]);
-        }
-        // hidden layer in two halves of four n-tiles (fewer live accumulators)
-        float pa = 0.f, pb = 0.f;
 #pragma unroll
-        for (int jh = 0; jh < 2; jh++) {
-            float acc[4][4];
-#pragma unroll
-            for (int jj = 0; jj < 4; jj++) {
-                const int j = 4 * jh + jj;
-                acc[jj][0] = acc[jj][2] = w.b2[8 * j + 2 * t];
-                acc[jj][1] = acc[jj][3] = w.b2[8 * j + 2 * t + 1];
-            }
-#pragma unroll
-            for (int kk = 0; kk < 4; kk++) {
-#pragma unroll
-                for (int jj = 0; jj < 4; jj++) {
-                    const int j = 4 * jh + jj;
-                    const __nv_bfloat16 *row = w.W2 + (8 * j + g) * NH + 16 * kk + 2 * t;
-                    unsigned b0 = *reinterpret_cast<const unsigned *>(row);
-                    unsigned b1 = *reinterpret_cast<const unsigned *>(row + 8);
-                    mma_bf16(acc[jj], A[kk], b0, b1);
-                }
-            }
-#pragma unroll
-            for (int jj = 0; jj < 4; jj++) {
-                const int j = 4 * jh + jj;
-#pragma unroll
-                for (int e = 0; e < 2; e++) {
-                    const float w3 = w.w3[8 * j + 2 * t + e];
-                    pa = fmaf(w3, tanh_fast(acc[jj][e]), pa);
-                    pb = fmaf(w3, tanh_fast(acc[jj][2 + e]), pb);
-                }
+            for (int mt = 0; mt < 2; mt++) {
+                A[mt][kk][2 * hi + 0] = pack_bf16(h[2 * mt][0], h[2 * mt][1]);          // row g
+                A[mt][kk][2 * hi + 1] = pack_bf16(h[2 * mt + 1][0], h[2 * mt + 1][1]);  // row g + 8
             }
         }
-        pa += __shfl_xor_sync(FULL, pa, 1);
-        pa += __shfl_xor_sync(FULL, pa, 2);
-        pb += __shfl_xor_sync(FULL, pb, 1);
-        pb += __shfl_xor_sync(FULL, pb, 2);
-        ysel[mt][0] = pa + w.b3;
-        ysel[mt][1] = pb + w.b3;
     }
-    // sample s = lane: m-tile s/16, row r = s%16 -> quad 4 (r%8), half r/8
-    const int r = lane & 15, src = 4 * (r & 7);
-    float v00 = __shfl_sync(FULL, ysel[0][0], src), v01 = __shfl_sync(FULL, ysel[0][1], src);
-    float v10 = __shfl_sync(FULL, ysel[1][0], src), v11 = __shfl_sync(FULL, ysel[1][1], src);
-    const bool upper = lane >= 16, half = r >= 8;
-    return upper ? (half ? v11 : v10) : (half ? v01 : v00);
+    float p[4] = {0.f, 0.f, 0.f, 0.f};  // partial y of samples g, g + 8, g + 16, g + 24
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+        const int col = 8 * nt + 2 * t;
+        const float2 b2 = *reinterpret_cast<const float2 *>(&w.b2[col]);
+        const float2 w3 = *reinterpret_cast<const float2 *>(&w.w3[col]);
+        float acc[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+            acc[mt][0] = acc[mt][2] = b2.x;
+            acc[mt][1] = acc[mt][3] = b2.y;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+            const uint2 b = w.W2F[nt][kk][lane];
+            mma_bf16(acc[0], A[0][kk], b.x, b.y);
+            mma_bf16(acc[1], A[1][kk], b.x, b.y);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+            p[2 * mt] = fmaf(w3.x, tanh_fast(acc[mt][0]), p[2 * mt]);
+            p[2 * mt] = fmaf(w3.y, tanh_fast(acc[mt][1]), p[2 * mt]);
+            p[2 * mt + 1] = fmaf(w3.x, tanh_fast(acc[mt][2]), p[2 * mt + 1]);
+            p[2 * mt + 1] = fmaf(w3.y, tanh_fast(acc[mt][3]), p[2 * mt + 1]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        p[r] += __shfl_xor_sync(FULL, p[r], 1);
+        p[r] += __shfl_xor_sync(FULL, p[r], 2);
+    }
+    // sample s = lane sits in row s & 7 of quad s >> 3, held by lane 4 (s & 7)
+    const int src = 4 * (lane & 7), q = lane >> 3;
+    float v[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) v[r] = __shfl_sync(FULL, p[r], src);
+    return (q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3]) + w.b3;
 }
 
-__device__ __forceinline__ void load_mlp_shared(MlpDev &sw, const MlpDev *w)
+// the inference prefix of the parameters into shared memory (sw: MLP_INFER_BYTES,
+// 16-byte aligned); the block synchronises before returning
+__device__ __forceinline__ const MlpDev &load_mlp_shared(unsigned char *sw, const MlpDev *w)
 {
     const int4 *src = reinterpret_cast<const int4 *>(w);
-    int4 *dst = reinterpret_cast<int4 *>(&sw);
-    for (int q = threadIdx.x; q < (int)(sizeof(MlpDev) / 16); q += blockDim.x) dst[q] = src[q];
+    int4 *dst = reinterpret_cast<int4 *>(sw);
+    for (int q = threadIdx.x; q < MLP_INFER_BYTES / 16; q += blockDim.x) dst[q] = src[q];
     __syncthreads();
+    return *reinterpret_cast<const MlpDev *>(sw);
 }
 
 }  // namespace echo
