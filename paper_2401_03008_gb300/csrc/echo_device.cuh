@@ -92,6 +92,16 @@ __device__ __forceinline__ long shifted(const Grid &g, int i, int j, int k, int 
     return lin(g, i, j, k);
 }
 
+// 32-bit linear index of the cell s steps from cell c along direction D (iD: the
+// cell's coordinate along D), wrapped; the library keeps grids below 2^31 cells
+template <int D>
+__device__ __forceinline__ int sidx(const Grid &g, int c, int iD, int s)
+{
+    const int nD = D == 0 ? g.nx : (D == 1 ? g.ny : g.nz);
+    const int stride = D == 0 ? 1 : (D == 1 ? g.nx : g.nx * g.ny);
+    return c + (wrapi(iD + s, nD) - iD) * stride;
+}
+
 __device__ __forceinline__ long shifted_rt(const Grid &g, int i, int j, int k, int d, int s)
 {
     if (d == 0) i = wrapi(i + s, g.nx);
@@ -165,7 +175,9 @@ template <typename R>
 __device__ __forceinline__ bool mp5_smooth(R um2, R um1, R u0, R up1, R up2, R &uor)
 {
     const R alpha = R(4);
-    uor = (R(3) * um2 - R(20) * um1 + R(90) * u0 + R(60) * up1 - R(5) * up2) * R(0.0078125);
+    // the weights over 128 are exact binary fractions: no separate scaling
+    uor = R(0.0234375) * um2 - R(0.15625) * um1 + R(0.703125) * u0 + R(0.46875) * up1 -
+          R(0.0390625) * up2;
     R ump = u0 + minmod2(up1 - u0, alpha * (u0 - um1));
     return le((uor - u0) * (uor - ump), R(1e-10));
 }
@@ -214,12 +226,23 @@ struct Mp5Queue {
     {
         if (threadIdx.x == 0) count = 0;
     }
-    // value of the reconstruction in slot k of this thread (placeholder if queued)
+    // value of the reconstruction in slot k of this thread (placeholder if queued).
+    // The lanes of a warp that need the limiter take consecutive entries with one
+    // shared-memory atomic per warp; a warp whose lanes are all smooth skips the
+    // queue on a warp-uniform branch.
     __device__ __forceinline__ R defer(R um2, R um1, R u0, R up1, R up2, int k, unsigned &mask)
     {
         R uor;
-        if (mp5_smooth(um2, um1, u0, up1, up2, uor)) return uor;
-        int e = atomicAdd(&count, 1);
+        const bool smooth = mp5_smooth(um2, um1, u0, up1, up2, uor);
+        const unsigned am = __activemask();
+        const unsigned need = __ballot_sync(am, !smooth);
+        if (need == 0u) return uor;
+        const int lane = threadIdx.x & 31, leader = __ffs(need) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&count, __popc(need));
+        base = __shfl_sync(am, base, leader);
+        if (smooth) return uor;
+        const int e = base + __popc(need & ((1u << lane) - 1u));
         if (e < QMAX) {
             val[e][0] = um2;
             val[e][1] = um1;
@@ -330,12 +353,16 @@ __device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &l
     R ex = -(vy * bz - vz * by);
     R ey = -(vz * bx - vx * bz);
     R ez = -(vx * by - vy * bx);
-    R e2 = ex * ex + ey * ey + ez * ez;
     R b2 = bx * bx + by * by + bz * bz;
+    R vb = vx * bx + vy * by + vz * bz;
+    // |v x B|^2 = v^2 B^2 - (v.B)^2 and E x B = B^2 v - (v.B) B (Lagrange and
+    // triple-product identities): fewer operations than from the components
+    R e2 = v2 * b2 - vb * vb;
     R D0 = rho * lor;
-    R Sx = w * vx + (ey * bz - ez * by);
-    R Sy = w * vy + (ez * bx - ex * bz);
-    R Sz = w * vz + (ex * by - ey * bx);
+    R wb = w + b2;
+    R Sx = wb * vx - vb * bx;
+    R Sy = wb * vy - vb * by;
+    R Sz = wb * vz - vb * bz;
     R ptot = pg + R(0.5) * (e2 + b2);
     U[0] = D0;
     U[1] = Sx;
@@ -358,19 +385,26 @@ __device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &l
     F[7] = vd * bz - vz * Bd;
     // approximate fast magnetosonic speeds; 1/rhoh and 1/(rhoh + b^2) from one
     // reciprocal of their product
-    R vb = vx * bx + vy * by + vz * bz;
     R bb2 = b2 * omv2 + vb * vb;
     R den = rhoh + bb2;
     R rr = R(1) / (rhoh * den);
     R cs2 = gam * pg * den * rr;
     R ca2 = bb2 * rhoh * rr;
     R w2 = cs2 + ca2 - cs2 * ca2;
-    R disc = w2 * omv2 * ((R(1) - v2 * w2) - vd * vd * (R(1) - w2));
-    disc = ltz(disc) ? R(0) : disc;
-    R sr = sqrt(disc);
-    R inv = R(1) / (R(1) - v2 * w2);
-    lp = (vd * (R(1) - w2) + sr) * inv;
-    lm = (vd * (R(1) - w2) - sr) * inv;
+    R X = R(1) - v2 * w2;
+    R disc = w2 * omv2 * (X - vd * vd * (R(1) - w2));
+    // sqrt(disc)/X and 1/X from one reciprocal square root q = 1/sqrt(disc X^2):
+    // sqrt(disc)/X = disc q and 1/X = X disc q^2 (disc > 0); disc = 0 takes 1/X
+    const R a = vd * (R(1) - w2);
+    if (gtz(disc)) {
+        R q = rsqrt(disc * X * X);
+        R srx = disc * q;
+        R inv = X * srx * q;
+        lp = a * inv + srx;
+        lm = a * inv - srx;
+    } else {
+        lp = lm = a / X;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -155,7 +155,7 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
     long f = blockIdx.x * (long)BS + threadIdx.x;
     const bool active = f < n;
     R amax = R(0);
-    long cs[6];
+    int cs[6];
     R L[8], Rt[8];
     unsigned mask = 0;
     bool own = false;  // face i+1/2 belongs to cell i
@@ -163,21 +163,23 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
         int i, j, k;
         coords(g, f, i, j, k);
         own = owned(g, i, j, k);
+        const int iD = D == 0 ? i : (D == 1 ? j : k);
 #pragma unroll
-        for (int m = 0; m < 6; m++) cs[m] = shifted<D>(g, i, j, k, m - 2);
+        for (int m = 0; m < 6; m++) cs[m] = sidx<D>(g, (int)f, iD, m - 2);
 #pragma unroll
         for (int v = 0; v < 8; v++) {
             // with UCT the normal field is the staggered face value, not reconstructed
             if (v == 5 + D && uct) continue;
             R s[6];
+            const R *pv = prim + v * n;
             if (g.rec) {  // linear: cells i-1 .. i+2
 #pragma unroll
-                for (int m = 1; m < 5; m++) s[m] = ld(prim + v * n + cs[m]);
+                for (int m = 1; m < 5; m++) s[m] = ld(pv + cs[m]);
                 L[v] = mc_val(s[1], s[2], s[3]);
                 Rt[v] = mc_val(s[4], s[3], s[2]);
             } else {
 #pragma unroll
-                for (int m = 0; m < 6; m++) s[m] = ld(prim + v * n + cs[m]);
+                for (int m = 0; m < 6; m++) s[m] = ld(pv + cs[m]);
                 L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], 2 * v, mask);
                 Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], 2 * v + 1, mask);
             }
@@ -276,9 +278,10 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
     if (c >= n) return;
     int i, j, k;
     coords(g, c, i, j, k);
-    long fs[6];
+    const int iD = D == 0 ? i : (D == 1 ? j : k);
+    int fs[6];
 #pragma unroll
-    for (int m = 0; m < 6; m++) fs[m] = shifted<D>(g, i, j, k, m - 3);
+    for (int m = 0; m < 6; m++) fs[m] = sidx<D>(g, (int)c, iD, m - 3);
     const R ih = (R)g.inv_h[D];
     const int ncomp = g.uct ? 5 : 8;
 #pragma unroll
@@ -286,7 +289,7 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
         if (q >= ncomp) break;
         R s[6];
 #pragma unroll
-        for (int m = 0; m < 6; m++) s[m] = ld(flux + q * n + fs[m]);
+        for (int m = 0; m < 6; m++) s[m] = ld(flux + q * n + (long)fs[m]);
         R d = der_c(s, ih, g.ho);
         rhs[q * n + c] = first ? -d : rhs[q * n + c] - d;
     }
@@ -311,7 +314,7 @@ k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__re
     // slots: va[s][t] = 4 s + t, vb[s][t] = 4 s + 2 + t, Ba[t] = 8 + t, Bb[s] = 10 + s
     R r[12];
     unsigned mask = 0;
-    long sb[6], sa[6];
+    int sb[6], sa[6];
     const int lin = g.rec;
     // left/right states of one stencil into slots k, k+1 of r
     auto recon = [&](const R *s, int k) {
@@ -326,10 +329,11 @@ k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__re
     if (active) {
         int i, j, k;
         coords(g, e, i, j, k);
+        const int iA = A == 0 ? i : (A == 1 ? j : k), iB = B == 0 ? i : (B == 1 ? j : k);
 #pragma unroll
         for (int m = 0; m < 6; m++) {
-            sb[m] = shifted<B>(g, i, j, k, m - 2);
-            sa[m] = shifted<A>(g, i, j, k, m - 2);
+            sb[m] = sidx<B>(g, (int)e, iB, m - 2);
+            sa[m] = sidx<A>(g, (int)e, iA, m - 2);
         }
         R s[6];
 #pragma unroll
