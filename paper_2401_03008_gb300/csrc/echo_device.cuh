@@ -383,27 +383,31 @@ __device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &l
     F[5] = vd * bx - vx * Bd;
     F[6] = vd * by - vy * Bd;
     F[7] = vd * bz - vz * Bd;
-    // approximate fast magnetosonic speeds; 1/rhoh and 1/(rhoh + b^2) from one
-    // reciprocal of their product
+    // Approximate fast magnetosonic speeds
+    //   lambda = [v_d (1 - w2) +- sqrt(w2 (1 - v^2) ((1 - v^2 w2) - v_d^2 (1 - w2)))] / (1 - v^2 w2)
+    // with cs2 = gam p / rho h, ca2 = b^2 / (rho h + b^2), w2 = cs2 + ca2 - cs2 ca2.
+    // Since 1 - w2 = (1 - cs2)(1 - ca2) = P / den and w2 = Q / den with
+    // P = rho h - gam p, Q = b^2 + gam p, den = rho h + b^2, multiplying through by den
+    // leaves lambda = [v_d P +- sqrt((1 - v^2) Q K)] / Y, Y = den - v^2 Q,
+    // K = Y - v_d^2 P: no reciprocal of rho h or den at all.
     R bb2 = b2 * omv2 + vb * vb;
-    R den = rhoh + bb2;
-    R rr = R(1) / (rhoh * den);
-    R cs2 = gam * pg * den * rr;
-    R ca2 = bb2 * rhoh * rr;
-    R w2 = cs2 + ca2 - cs2 * ca2;
-    R X = R(1) - v2 * w2;
-    R disc = w2 * omv2 * (X - vd * vd * (R(1) - w2));
-    // sqrt(disc)/X and 1/X from one reciprocal square root q = 1/sqrt(disc X^2):
-    // sqrt(disc)/X = disc q and 1/X = X disc q^2 (disc > 0); disc = 0 takes 1/X
-    const R a = vd * (R(1) - w2);
+    R gp = gam * pg;
+    R P = rhoh - gp;
+    R Q = bb2 + gp;
+    R Y = (rhoh + bb2) - v2 * Q;
+    R K = Y - vd * vd * P;
+    R disc = omv2 * Q * K;
+    // sqrt(disc)/Y and 1/Y from one reciprocal square root q = 1/sqrt(disc Y^2):
+    // sqrt(disc)/Y = disc q and 1/Y = Y disc q^2 (disc > 0); disc <= 0 takes 1/Y
+    const R a = vd * P;
     if (gtz(disc)) {
-        R q = rsqrt(disc * X * X);
+        R q = rsqrt(disc * Y * Y);
         R srx = disc * q;
-        R inv = X * srx * q;
+        R inv = Y * srx * q;
         lp = a * inv + srx;
         lm = a * inv - srx;
     } else {
-        lp = lm = a / X;
+        lp = lm = a / Y;
     }
 }
 
