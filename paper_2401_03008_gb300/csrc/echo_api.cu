@@ -193,6 +193,8 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     g.hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
     g.gam = cfg->gamma_ad;
     g.gfac = cfg->gamma_ad / (cfg->gamma_ad - 1.0);
+    g.gm1g = (cfg->gamma_ad - 1.0) / cfg->gamma_ad;
+    g.gm1g32 = (float)g.gm1g;
     g.ho = cfg->ho;
     g.uct = cfg->uct;
     g.rec = cfg->rec;

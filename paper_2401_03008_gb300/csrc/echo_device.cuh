@@ -20,6 +20,8 @@ struct Grid {
     double hmin;
     double gam;        // adiabatic index
     double gfac;       // gam / (gam - 1)
+    double gm1g;       // (gam - 1) / gam
+    float gm1g32;      // the same in FP32 (the mixed path's FP32 pre-iterations)
     int ho;            // high-order INT / DER
     int uct;           // 1: staggered field + UCT; 0: cell-centred field, 8-component HLL
     int rec;           // 0: MP5; 1: linear with the MC limiter
@@ -297,26 +299,34 @@ __device__ __forceinline__ R int_c(R a, R b, R c, R d, int ho)
 // cell-centred field at cell c: INT of the staggered components (UCT) or the cell
 // values themselves (UCT off)
 template <typename BT>
+__device__ __forceinline__ BT cell_field_t(const Grid &g, const BT *__restrict__ Bf, long c,
+                                           int i, int j, int k, int d)
+{
+    const BT *b = Bf + d * g.n;
+    if (!g.uct) return b[c];
+    const int ci = (int)c;
+    int sm2, sm1, sp1;
+    if (d == 0) {
+        sm2 = sidx<0>(g, ci, i, -2);
+        sm1 = sidx<0>(g, ci, i, -1);
+        sp1 = sidx<0>(g, ci, i, 1);
+    } else if (d == 1) {
+        sm2 = sidx<1>(g, ci, j, -2);
+        sm1 = sidx<1>(g, ci, j, -1);
+        sp1 = sidx<1>(g, ci, j, 1);
+    } else {
+        sm2 = sidx<2>(g, ci, k, -2);
+        sm1 = sidx<2>(g, ci, k, -1);
+        sp1 = sidx<2>(g, ci, k, 1);
+    }
+    return int_c(b[sm2], b[sm1], b[c], b[sp1], g.ho);
+}
+
+template <typename BT>
 __device__ __forceinline__ double cell_field(const Grid &g, const BT *__restrict__ Bf, long c,
                                              int i, int j, int k, int d)
 {
-    const BT *b = Bf + d * g.n;
-    if (!g.uct) return (double)b[c];
-    long sm2, sm1, sp1;
-    if (d == 0) {
-        sm2 = lin(g, wrapi(i - 2, g.nx), j, k);
-        sm1 = lin(g, wrapi(i - 1, g.nx), j, k);
-        sp1 = lin(g, wrapi(i + 1, g.nx), j, k);
-    } else if (d == 1) {
-        sm2 = lin(g, i, wrapi(j - 2, g.ny), k);
-        sm1 = lin(g, i, wrapi(j - 1, g.ny), k);
-        sp1 = lin(g, i, wrapi(j + 1, g.ny), k);
-    } else {
-        sm2 = lin(g, i, j, wrapi(k - 2, g.nz));
-        sm1 = lin(g, i, j, wrapi(k - 1, g.nz));
-        sp1 = lin(g, i, j, wrapi(k + 1, g.nz));
-    }
-    return (double)int_c(b[sm2], b[sm1], b[c], b[sp1], g.ho);
+    return (double)cell_field_t(g, Bf, c, i, j, k, d);
 }
 
 // DER: derivative at a centre from staggered values s[0..5] at i-5/2..i+5/2.
@@ -454,6 +464,7 @@ __device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const
 // ---------------------------------------------------------------------------
 struct C2PInv {
     double D, S2, B2, SB, U, gm1g;
+    float gm1g32;
 };
 
 // v^2(W) and r = 1/(W (W + B^2)); valid when W > 0, finite and v^2 < 1
@@ -480,7 +491,7 @@ __device__ __forceinline__ bool c2p_ok(const C2PInv &q, double W)
 __device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &iters, float &idf)
 {
     const float D = (float)q.D, S2 = (float)q.S2, B2 = (float)q.B2, SB = (float)q.SB;
-    const float U = (float)q.U, gm1g = (float)q.gm1g, SB2 = SB * SB;
+    const float U = (float)q.U, gm1g = q.gm1g32, SB2 = SB * SB;
     float W = (float)W0;
     iters = 0;
     idf = 0.f;
@@ -521,9 +532,10 @@ __device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &ite
 // point computes v^2 and 1/(W (W+B^2)) there, and the next iteration reuses both,
 // so an iteration costs two divisions and one reciprocal square root.
 // Returns true on success.  prim = (rho, vx, vy, vz, p); B the cell-centred field.
-__device__ __forceinline__ bool c2p_newton(const double *u, const double *B, double gam,
-                                           double W0, double tol, int maxit, double *prim,
-                                           double &Wout, int &iters, int pre32, int &iters32)
+__device__ __forceinline__ bool c2p_newton(const double *u, const double *B, double gm1g,
+                                           float gm1g32, double W0, double tol, int maxit,
+                                           double *prim, double &Wout, int &iters, int pre32,
+                                           int &iters32)
 {
     C2PInv q;
     q.D = u[0];
@@ -531,7 +543,8 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     q.B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     q.SB = u[1] * B[0] + u[2] * B[1] + u[3] * B[2];
     q.U = u[4];
-    q.gm1g = (gam - 1.0) / gam;
+    q.gm1g = gm1g;  // (gam - 1)/gam, formed once on the host
+    q.gm1g32 = gm1g32;
     const double SB2 = q.SB * q.SB;
     iters32 = 0;
     // mixed path: FP32 iterations first; their last derivative then serves every
@@ -540,6 +553,7 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     float idf32 = 0.f;
     if (pre32) W0 = c2p_pre32(q, W0, iters32, idf32);
     const bool chord = idf32 != 0.f;
+    const double idf = (double)idf32;
     double W = W0, v2 = 0.0, r = 0.0;
     bool ok = c2p_eval(q, W, v2, r);
     for (int k = 0; k < 64 && !ok; k++) {
@@ -559,7 +573,7 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
         double f = W - p + 0.5 * (1.0 + v2) * q.B2 - 0.5 * SB2 * iW2 - q.U;
         double dW;
         if (chord) {
-            dW = -f * (double)idf32;
+            dW = -f * idf;
         } else {
             double dv2 = -2.0 * SB2 * (iW2 * iW) * iwb - 2.0 * v2 * iwb;
             double dp = q.gm1g * (omv2 - W * dv2 + 0.5 * q.D * dv2 * isq);

@@ -70,7 +70,7 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
         }
         double p[5], Wn;
         int iters, iters32;
-        bad = !c2p_newton(u, B, g.gam, W0, par.tol, par.maxit, p, Wn, iters, par.pre32, iters32);
+        bad = !c2p_newton(u, B, g.gm1g, g.gm1g32, W0, par.tol, par.maxit, p, Wn, iters, par.pre32, iters32);
         it = (unsigned)iters;
         it32 = (unsigned)iters32;
 #pragma unroll

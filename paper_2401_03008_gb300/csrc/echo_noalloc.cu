@@ -190,6 +190,8 @@ echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, i
     g.hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
     g.gam = 0.0;
     g.gfac = 0.0;
+    g.gm1g = 0.0;
+    g.gm1g32 = 0.f;
     g.ho = ho;
     g.uct = 1;
     g.rec = 0;
