@@ -195,6 +195,9 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     g.gfac = cfg->gamma_ad / (cfg->gamma_ad - 1.0);
     g.gm1g = (cfg->gamma_ad - 1.0) / cfg->gamma_ad;
     g.gm1g32 = (float)g.gm1g;
+    g.gam32 = (float)g.gam;
+    g.gfac32 = (float)g.gfac;
+    for (int d = 0; d < 3; d++) g.inv_h32[d] = (float)g.inv_h[d];
     g.ho = cfg->ho;
     g.uct = cfg->uct;
     g.rec = cfg->rec;

@@ -327,6 +327,7 @@ echo_status echo_decomp_create(const echo_config *cfg, int px, int py, int pz, i
         for (int a = 0; a < 3; a++) {
             c->g.h[a] = h[a];
             c->g.inv_h[a] = 1.0 / h[a];
+            c->g.inv_h32[a] = (float)c->g.inv_h[a];
             c->g.lo[a] = gm.G[a];
             c->g.hi[a] = gm.G[a] + gm.nloc[a];
         }

@@ -9,6 +9,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "echo_convert.cuh"
+
 namespace echo {
 
 // Grid description passed by value to every kernel.
@@ -21,7 +23,9 @@ struct Grid {
     double gam;        // adiabatic index
     double gfac;       // gam / (gam - 1)
     double gm1g;       // (gam - 1) / gam
-    float gm1g32;      // the same in FP32 (the mixed path's FP32 pre-iterations)
+    // FP32 copies of the constants the mixed path's FP32 kernels use (a conversion
+    // in the kernel would issue on the FP64 pipe)
+    float gm1g32, gam32, gfac32, inv_h32[3];
     int ho;            // high-order INT / DER
     int uct;           // 1: staggered field + UCT; 0: cell-centred field, 8-component HLL
     int rec;           // 0: MP5; 1: linear with the MC limiter
@@ -31,6 +35,16 @@ struct Grid {
     int lo[3], hi[3];
     int primary;       // 1: this grid advances the step counter
 };
+
+// a grid constant in the precision R (the FP32 copy for float)
+template <typename R> __device__ __forceinline__ R gconst(double d, float f);
+template <> __device__ __forceinline__ double gconst<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float gconst<float>(double, float f) { return f; }
+
+// a double in the precision R, rounded to nearest (integer pipe for float)
+template <typename R> __device__ __forceinline__ R to_r(double x);
+template <> __device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_r<float>(double x) { return to_f32(x); }
 
 __device__ __forceinline__ bool owned(const Grid &g, int i, int j, int k)
 {
@@ -326,7 +340,7 @@ template <typename BT>
 __device__ __forceinline__ double cell_field(const Grid &g, const BT *__restrict__ Bf, long c,
                                              int i, int j, int k, int d)
 {
-    return (double)cell_field_t(g, Bf, c, i, j, k, d);
+    return to_f64(cell_field_t(g, Bf, c, i, j, k, d));
 }
 
 // DER: derivative at a centre from staggered values s[0..5] at i-5/2..i+5/2.
@@ -490,9 +504,9 @@ __device__ __forceinline__ bool c2p_ok(const C2PInv &q, double W)
 // is not finite.  The FP64 iteration that follows decides the result.
 __device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &iters, float &idf)
 {
-    const float D = (float)q.D, S2 = (float)q.S2, B2 = (float)q.B2, SB = (float)q.SB;
-    const float U = (float)q.U, gm1g = q.gm1g32, SB2 = SB * SB;
-    float W = (float)W0;
+    const float D = to_f32(q.D), S2 = to_f32(q.S2), B2 = to_f32(q.B2), SB = to_f32(q.SB);
+    const float U = to_f32(q.U), gm1g = q.gm1g32, SB2 = SB * SB;
+    float W = to_f32(W0);
     iters = 0;
     idf = 0.f;
     if (!(W > 0.f) || !isfinite(W)) return W0;
@@ -523,7 +537,7 @@ __device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &ite
         idf = rdf;
         if (fabsf(dW) <= 4e-6f * W) break;
     }
-    return (double)W;
+    return to_f64(W);
 }
 
 // Newton on f(W) = W - p(W) + (1 + v^2) B^2/2 - (S.B)^2/(2 W^2) - U with the
@@ -553,7 +567,7 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     float idf32 = 0.f;
     if (pre32) W0 = c2p_pre32(q, W0, iters32, idf32);
     const bool chord = idf32 != 0.f;
-    const double idf = (double)idf32;
+    const double idf = to_f64(idf32);
     double W = W0, v2 = 0.0, r = 0.0;
     bool ok = c2p_eval(q, W, v2, r);
     for (int k = 0; k < 64 && !ok; k++) {

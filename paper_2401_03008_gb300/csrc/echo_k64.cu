@@ -91,7 +91,7 @@ void launch_copy_state(echo_ctx *c, double *dst_u, double *dst_b, const double *
 __global__ void __launch_bounds__(BS) k_to_float(long m, const double *__restrict__ in, float *__restrict__ out)
 {
     long q = blockIdx.x * (long)BS + threadIdx.x;
-    if (q < m) out[q] = (float)in[q];
+    if (q < m) out[q] = to_f32(in[q]);
 }
 
 void launch_bf32(echo_ctx *c)

@@ -52,7 +52,7 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
         for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
         double W0;
         if (guess) {
-            W0 = (double)guess[c];
+            W0 = to_f64(guess[c]);
             C2PInv q;
             q.D = u[0];
             q.S2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
@@ -74,9 +74,9 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
         it = (unsigned)iters;
         it32 = (unsigned)iters32;
 #pragma unroll
-        for (int v = 0; v < 5; v++) prim[v * n + c] = (R)p[v];
+        for (int v = 0; v < 5; v++) prim[v * n + c] = to_r<R>(p[v]);
 #pragma unroll
-        for (int v = 0; v < 3; v++) prim[(5 + v) * n + c] = (R)B[v];
+        for (int v = 0; v < 3; v++) prim[(5 + v) * n + c] = to_r<R>(B[v]);
         if (update_w) W[c] = Wn;
         if (!own) {  // a neighbour's cell: updated, not counted
             it = it32 = 0;
@@ -131,7 +131,7 @@ k_mlp_guess(Grid g, const double *__restrict__ U, const BT *__restrict__ Bf,
         float x[NIN];
         mlp_features(u, B, x);
         const float y = mlp_warp_forward(sw, x, lane);
-        if (c < n) guess[c] = (float)(u[4] * (double)y);
+        if (c < n) guess[c] = to_f32(u[4] * to_f64(y));
     }
 }
 
@@ -218,8 +218,8 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
             }
         }
         if (nfb && own) atomicAdd(&sc->rec_fallbacks, (unsigned)nfb);
-        const R gam = (R)g.gam;
-        const R gfac = (R)g.gfac;
+        const R gam = gconst<R>(g.gam, g.gam32);
+        const R gfac = gconst<R>(g.gfac, g.gfac32);
         R UL[8], FL[8], UR[8], FR[8], lmL, lpL, lmR, lpR;
         phys<R, D>(L, gam, gfac, UL, FL, lmL, lpL);
         phys<R, D>(Rt, gam, gfac, UR, FR, lmR, lpR);
@@ -282,7 +282,7 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
     int fs[6];
 #pragma unroll
     for (int m = 0; m < 6; m++) fs[m] = sidx<D>(g, (int)c, iD, m - 3);
-    const R ih = (R)g.inv_h[D];
+    const R ih = gconst<R>(g.inv_h[D], g.inv_h32[D]);
     const int ncomp = g.uct ? 5 : 8;
 #pragma unroll
     for (int q = 0; q < 8; q++) {
@@ -382,7 +382,8 @@ __device__ __forceinline__ R curl_a(const Grid &g, const R *__restrict__ E, int 
         s[m] = ld(E + c * n + shifted_rt(g, i, j, k, b, m - 3));
         t[m] = ld(E + b * n + shifted_rt(g, i, j, k, c, m - 3));
     }
-    return der_c(s, (R)g.inv_h[b], g.ho) - der_c(t, (R)g.inv_h[c], g.ho);
+    return der_c(s, gconst<R>(g.inv_h[b], g.inv_h32[b]), g.ho) -
+           der_c(t, gconst<R>(g.inv_h[c], g.inv_h32[c]), g.ho);
 }
 
 // ---------------------------------------------------------------------------
@@ -405,11 +406,11 @@ k_rk(Grid g, int stage, int last, double a0, const R *__restrict__ E, const R *_
         for (int v = 0; v < 8; v++) {
             double r, u, *pu, *pu0;
             if (v < 5) {
-                r = (double)rhs[v * n + c];
+                r = to_f64(rhs[v * n + c]);
                 pu = U + v * n + c;
                 pu0 = U0 + v * n + c;
             } else {
-                r = g.uct ? -(double)curl_a(g, E, v - 5, i, j, k) : (double)rhs[v * n + c];
+                r = g.uct ? -to_f64(curl_a(g, E, v - 5, i, j, k)) : to_f64(rhs[v * n + c]);
                 pu = Bf + (v - 5) * n + c;
                 pu0 = Bf0 + (v - 5) * n + c;
             }
@@ -424,7 +425,7 @@ k_rk(Grid g, int stage, int last, double a0, const R *__restrict__ E, const R *_
                 un = (*pu0) * a0 + (1.0 - a0) * (u + dt * r);
             }
             *pu = un;
-            if (v >= 5 && Bf32) Bf32[(v - 5) * n + c] = (float)un;
+            if (v >= 5 && Bf32) Bf32[(v - 5) * n + c] = to_f32(un);
         }
     }
     if (last && g.primary && blockIdx.x == 0 && threadIdx.x == 0) sc->step += 1;
@@ -442,7 +443,7 @@ k_curl(Grid g, const R *__restrict__ E, double *__restrict__ out, double sign, i
     coords(g, c, i, j, k);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        double v = sign * (double)curl_a(g, E, a, i, j, k);
+        double v = sign * to_f64(curl_a(g, E, a, i, j, k));
         out[a * n + c] = accumulate ? out[a * n + c] + v : v;
     }
 }
@@ -451,7 +452,7 @@ template <typename R>
 __global__ void __launch_bounds__(BS) k_to_double(long m, const R *__restrict__ in, double *__restrict__ out)
 {
     long q = blockIdx.x * (long)BS + threadIdx.x;
-    if (q < m) out[q] = (double)in[q];
+    if (q < m) out[q] = to_f64(in[q]);
 }
 
 // ---------------------------------------------------------------------------

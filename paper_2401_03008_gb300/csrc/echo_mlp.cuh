@@ -69,9 +69,9 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
 // features of one cell: D/U, S^2/U^2, B^2/U, (S.B)^2/(S^2 B^2), ln(U/D)
 __device__ __forceinline__ void mlp_features(const double *u, const double *B, float *x)
 {
-    float D = (float)u[0], U = (float)u[4];
-    float sx = (float)u[1], sy = (float)u[2], sz = (float)u[3];
-    float bx = (float)B[0], by = (float)B[1], bz = (float)B[2];
+    float D = to_f32(u[0]), U = to_f32(u[4]);
+    float sx = to_f32(u[1]), sy = to_f32(u[2]), sz = to_f32(u[3]);
+    float bx = to_f32(B[0]), by = to_f32(B[1]), bz = to_f32(B[2]);
     float S2 = sx * sx + sy * sy + sz * sz;
     float B2 = bx * bx + by * by + bz * bz;
     float SB = sx * bx + sy * by + sz * bz;

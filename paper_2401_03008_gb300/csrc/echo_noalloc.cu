@@ -191,7 +191,8 @@ echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, i
     g.gam = 0.0;
     g.gfac = 0.0;
     g.gm1g = 0.0;
-    g.gm1g32 = 0.f;
+    g.gm1g32 = g.gam32 = g.gfac32 = 0.f;
+    for (int d = 0; d < 3; d++) g.inv_h32[d] = (float)g.inv_h[d];
     g.ho = ho;
     g.uct = 1;
     g.rec = 0;
