@@ -542,7 +542,8 @@ __device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &ite
 
 // Newton on f(W) = W - p(W) + (1 + v^2) B^2/2 - (S.B)^2/(2 W^2) - U with the
 // analytic derivative; a trial point outside the domain halves the step; stop
-// after an undamped step with |dW| <= tol W and one more polishing step.  The domain check of a trial
+// after an undamped step with |dW| <= tol W and one more polishing step (the chord
+// iteration of the mixed path stops after that step).  The domain check of a trial
 // point computes v^2 and 1/(W (W+B^2)) there, and the next iteration reuses both,
 // so an iteration costs two divisions and one reciprocal square root.
 // Returns true on success.  prim = (rho, vx, vy, vz, p); B the cell-centred field.
@@ -615,7 +616,18 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
             conv = true;
             break;
         }
-        if (lam == 1.0 && le(step, tol * W)) polish = true;
+        if (lam == 1.0 && le(step, tol * W)) {
+            // A chord step contracts the error by the slope's relative error
+            // (<= ~1e-5 for an FP32-refined slope), so the error left after an undamped
+            // step of at most tol W is below 1e-5 tol W: the mixed path stops there,
+            // four orders of magnitude under the FP32 rounding of its sweeps.  Newton
+            // (FP64 path) takes the polishing step down to the rounding floor.
+            if (chord) {
+                conv = true;
+                break;
+            }
+            polish = true;
+        }
     }
     iters = it;
     Wout = W;
