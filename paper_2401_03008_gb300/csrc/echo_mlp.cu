@@ -95,18 +95,23 @@ k_mlp_harvest(Grid g, const double *__restrict__ U, const double *__restrict__ B
 
 // C[M][64] (FP32) = A[M][K] (bf16, row-major) x Bt[64][K]^T (bf16, row-major);
 // a block of 4 warps covers 64 rows, each warp 16 rows x 64 columns; M % 64 == 0,
-// K % 16 == 0.
+// K % 16 == 0.  With kchunk < K, block y takes the K range [y kchunk, (y+1) kchunk)
+// and adds its partial product into C (which the caller zeroes): the
+// back-propagation product dW2 = dZ2^T H1 has only 64 rows but the batch as K.
 __global__ void __launch_bounds__(128)
 k_gemm_bf16(int M, int K, const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ Bt,
-            float *__restrict__ C)
+            float *__restrict__ C, int kchunk = 0)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const long m0 = (long)blockIdx.x * 64 + warp * 16;
     if (m0 >= M) return;
+    const bool split = kchunk > 0;
+    const int kbeg = split ? blockIdx.y * kchunk : 0;
+    const int kend = split ? min(K, kbeg + kchunk) : K;
     float acc[8][4];
     for (int j = 0; j < 8; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = kbeg; k0 < kend; k0 += 16) {
         unsigned a[4];
         a[0] = *reinterpret_cast<const unsigned *>(A + (m0 + g) * K + k0 + 2 * t);
         a[1] = *reinterpret_cast<const unsigned *>(A + (m0 + g + 8) * K + k0 + 2 * t);
@@ -121,11 +126,25 @@ k_gemm_bf16(int M, int K, const __nv_bfloat16 *__restrict__ A, const __nv_bfloat
     for (int j = 0; j < 8; j++) {
         float *c0 = C + (m0 + g) * NH + 8 * j + 2 * t;
         float *c1 = C + (m0 + g + 8) * NH + 8 * j + 2 * t;
-        c0[0] = acc[j][0];
-        c0[1] = acc[j][1];
-        c1[0] = acc[j][2];
-        c1[1] = acc[j][3];
+        if (split) {
+            atomicAdd(c0, acc[j][0]);
+            atomicAdd(c0 + 1, acc[j][1]);
+            atomicAdd(c1, acc[j][2]);
+            atomicAdd(c1 + 1, acc[j][3]);
+        } else {
+            c0[0] = acc[j][0];
+            c0[1] = acc[j][1];
+            c1[0] = acc[j][2];
+            c1[1] = acc[j][3];
+        }
     }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 struct TrainBufs {
@@ -164,7 +183,9 @@ k_train_l1(int B, long n, long first, long P, long off, const float *__restrict_
     }
 }
 
-// output layer, loss and the gradients of w3, b3, b2; dz2 for the products
+// output layer, loss and the gradients of w3, b3, b2; dz2 for the products.  The
+// per-sample contributions are summed over each warp with shuffles first, so the
+// block's shared accumulators take one atomic per warp instead of one per sample.
 __global__ void __launch_bounds__(256)
 k_train_out(int B, const MlpDev *__restrict__ w, TrainBufs tb)
 {
@@ -172,21 +193,29 @@ k_train_out(int B, const MlpDev *__restrict__ w, TrainBufs tb)
     for (int q = threadIdx.x; q < 2 * NH + 2; q += blockDim.x) red[q] = 0.f;
     __syncthreads();
     const int s = blockIdx.x * 256 + threadIdx.x;
-    if (s < B) {
-        float h2[NH];
-        float y = w->b3;
-        for (int o = 0; o < NH; o++) {
-            h2[o] = tanhf(tb.Z2[s * NH + o] + w->b2[o]);
-            y = fmaf(w->w3[o], h2[o], y);
+    const bool act = s < B;
+    const bool lead = (threadIdx.x & 31) == 0;
+    float h2[NH];
+    float y = w->b3;
+    for (int o = 0; o < NH; o++) {
+        h2[o] = act ? tanhf(tb.Z2[s * NH + o] + w->b2[o]) : 0.f;
+        y = fmaf(w->w3[o], h2[o], y);
+    }
+    const float e = act ? y - tb.T[s] : 0.f;
+    const float dy = 2.f * e / (float)B;
+    const float se = warp_sum_f(e * e), sdy = warp_sum_f(dy);
+    if (lead) {
+        atomicAdd(&red[2 * NH], se);
+        atomicAdd(&red[2 * NH + 1], sdy);
+    }
+    for (int o = 0; o < NH; o++) {
+        const float dz = dy * w->w3[o] * (1.f - h2[o] * h2[o]);
+        const float a = warp_sum_f(dy * h2[o]), b = warp_sum_f(dz);
+        if (lead) {
+            atomicAdd(&red[o], a);
+            atomicAdd(&red[NH + o], b);
         }
-        const float e = y - tb.T[s];
-        const float dy = 2.f * e / (float)B;
-        atomicAdd(&red[2 * NH], e * e);
-        atomicAdd(&red[2 * NH + 1], dy);
-        for (int o = 0; o < NH; o++) {
-            const float dz = dy * w->w3[o] * (1.f - h2[o] * h2[o]);
-            atomicAdd(&red[o], dy * h2[o]);
-            atomicAdd(&red[NH + o], dz);
+        if (act) {
             __nv_bfloat16 db = __float2bfloat16_rn(dz);
             tb.DZ2[s * NH + o] = db;
             tb.DZ2T[(long)o * B + s] = db;
@@ -210,14 +239,21 @@ __global__ void __launch_bounds__(256) k_train_back1(int B, TrainBufs tb)
     for (int q = threadIdx.x; q < NH * NIN + NH; q += blockDim.x) red[q] = 0.f;
     __syncthreads();
     const int s = blockIdx.x * 256 + threadIdx.x;
-    if (s < B) {
-        float x[NIN];
-        for (int f = 0; f < NIN; f++) x[f] = tb.X[s * NIN + f];
-        for (int o = 0; o < NH; o++) {
+    const bool act = s < B;
+    const bool lead = (threadIdx.x & 31) == 0;
+    float x[NIN];
+    for (int f = 0; f < NIN; f++) x[f] = act ? tb.X[s * NIN + f] : 0.f;
+    for (int o = 0; o < NH; o++) {
+        float dz = 0.f;
+        if (act) {
             const float h = tb.H1f[s * NH + o];
-            const float dz = tb.DH1[s * NH + o] * (1.f - h * h);
-            atomicAdd(&red[NH * NIN + o], dz);
-            for (int f = 0; f < NIN; f++) atomicAdd(&red[o * NIN + f], dz * x[f]);
+            dz = tb.DH1[s * NH + o] * (1.f - h * h);
+        }
+        const float sb = warp_sum_f(dz);
+        if (lead) atomicAdd(&red[NH * NIN + o], sb);
+        for (int f = 0; f < NIN; f++) {
+            const float sw = warp_sum_f(dz * x[f]);
+            if (lead) atomicAdd(&red[o * NIN + f], sw);
         }
     }
     __syncthreads();
@@ -284,7 +320,9 @@ struct Trainer {
         k_train_l1<<<nb, 256, 0, s>>>(B, n, first, P, off, feats, target, w, tb);
         k_gemm_bf16<<<B / 64, 128, 0, s>>>(B, NH, tb.H1, w->W2, tb.Z2);
         k_train_out<<<nb, 256, 0, s>>>(B, w, tb);
-        k_gemm_bf16<<<1, 128, 0, s>>>(NH, B, tb.DZ2T, tb.H1T, tb.grad + O_W2);
+        const int kchunk = 256;
+        k_gemm_bf16<<<dim3(1, (B + kchunk - 1) / kchunk), 128, 0, s>>>(NH, B, tb.DZ2T, tb.H1T,
+                                                                      tb.grad + O_W2, kchunk);
         k_gemm_bf16<<<B / 64, 128, 0, s>>>(B, NH, tb.DZ2, w->W2T, tb.DH1);
         k_train_back1<<<nb, 256, 0, s>>>(B, tb);
     }
