@@ -17,6 +17,17 @@
 namespace echo {
 
 constexpr int BS = 256;
+// Resident blocks of 256 threads per SM asked of the compiler, per kernel and
+// precision (measured on the 256^3 bench; 1 = no request).  The FP32 sweeps are
+// issue- and latency-bound and gain from more warps despite a few spilled values
+// (6 blocks at 40 registers: 5.3e8 -> 5.7e8 cell-updates/s against 4 blocks at 64);
+// the FP32-path inversion and RK gain a little (3 %, 13 %).  The FP64 kernels are
+// bound by the FP64 pipe; three blocks (at most 85 registers) keep the compiler
+// from spending registers that would cost a block (flux sweep: 3 % faster).
+constexpr int minb_flux(int rbytes) { return rbytes == 4 ? 6 : 3; }
+constexpr int minb_uct(int rbytes) { return rbytes == 4 ? 6 : 3; }
+constexpr int minb_c2p(int rbytes) { return rbytes == 4 ? 4 : 3; }
+constexpr int minb_rk(int rbytes) { return rbytes == 4 ? 6 : 3; }
 
 template <typename R>
 __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
@@ -28,7 +39,7 @@ __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
 // that guess is selected, else NULL.  An unusable guess falls back to the previous
 // W and is counted.
 template <typename R>
-__global__ void __launch_bounds__(BS)
+__global__ void __launch_bounds__(BS, minb_c2p(sizeof(R)))
 k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
           double *__restrict__ W, const float *__restrict__ guess, R *__restrict__ prim,
           C2PParams par, DevScalars *sc, int stage, long step, int update_w, int count)
@@ -141,8 +152,9 @@ k_mlp_guess(Grid g, const double *__restrict__ U, const BT *__restrict__ Bf,
 // queue capacity of the deferred MP5 limiting: two entries per thread on average
 constexpr int QMAX = 2 * BS;
 
+
 template <typename R, int D>
-__global__ void __launch_bounds__(BS)
+__global__ void __launch_bounds__(BS, minb_flux(sizeof(R)))
 k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restrict__ flux,
        R *__restrict__ fd, DevScalars *sc, int want_amax)
 {
@@ -299,7 +311,7 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
 // step 4a: UCT edge field along C
 // ---------------------------------------------------------------------------
 template <typename R, int C>
-__global__ void __launch_bounds__(BS)
+__global__ void __launch_bounds__(BS, minb_uct(sizeof(R)))
 k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__restrict__ fdb,
       R *__restrict__ E, DevScalars *sc)
 {
@@ -390,7 +402,7 @@ __device__ __forceinline__ R curl_a(const Grid &g, const R *__restrict__ E, int 
 // step 4b + 5: curl of E and the SSP-RK3 stage on 5 cell + 3 face variables
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(BS)
+__global__ void __launch_bounds__(BS, minb_rk(sizeof(R)))
 k_rk(Grid g, int stage, int last, double a0, const R *__restrict__ E, const R *__restrict__ rhs,
      double *__restrict__ U, double *__restrict__ U0, double *__restrict__ Bf,
      double *__restrict__ Bf0, float *__restrict__ Bf32, DevScalars *sc)
