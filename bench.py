@@ -28,8 +28,8 @@ UNIT = "cell-updates/s"
 # of the launch.  Bytes: each array element read or written once (stencil
 # neighbours come from cache).  FLOPs: FP64 (or FP32 in the mixed path)
 # floating-point operations the algorithm performs per unit, an FMA counted as 2,
-# as counted by ncu (sass thread instructions, FP64 add/mul/fma) on the 256^3
-# workload; see the design doc.
+# as counted by ncu (sass thread instructions, FP64 add/mul/fma) at 96^3 and read
+# from profiles/flops_per_unit.json.
 R64, R32 = 8, 4
 
 

@@ -186,7 +186,7 @@ long echo_launches(const echo_ctx *ctx);
  * *flops (an FMA counts as 2).  precision: ECHO_FP64 or ECHO_MIXED (= FP32). */
 echo_status echo_probe_fma_peak(echo_ctx *ctx, int precision, double *flops);
 
-/* ---- The learned Newton starting guess (the benchmark spec's extension; the paper
+/* ---- The learned Newton starting guess (a service of this library; the paper
  * has no learned component).  Network 5 -> 64 -> 64 -> 1 with tanh hidden layers
  * on five rotation-invariant, dimensionless features of a cell's conserved state
  * (D/U, S^2/U^2, B^2/U, (S.B)^2/(S^2 B^2), ln(U/D)); output y = W/U and guess
