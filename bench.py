@@ -110,6 +110,19 @@ def dist_setup(args):
     return world, rank, local
 
 
+def job_rate(ms, units_per_rank, world, device="cuda"):
+    """The slowest rank's timed milliseconds (max over the process group) and the
+    whole-job rate: the units all ranks processed over that time.  Replicas share
+    no data; this reduction is the only collective of the run."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 def workload_state(n, wave, uct=1):
     from paper_2401_03008_gb300 import workloads as wl
     m = {"oblique": (1, 1, 1), "x": (1, 0, 0)}[wave]
@@ -256,12 +269,7 @@ def main():
     launches = s.launches - l0
     clocks = clk.stop()
     assert done == args.steps
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * n ** 3 * args.steps / (ms * 1e-3)
+    ms, value = job_rate(ms, n ** 3 * args.steps, world)
     diag = s.diagnostics()
     # FP64 state after warm-up + timed steps: the variants are compared with it
     ref = s.primitives() if (args.variants and args.precision == "fp64" and args.uct
