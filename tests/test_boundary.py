@@ -99,3 +99,26 @@ def test_decomp_rejects_bad_arguments(blocks, halo, guess):
     assert L.echo_decomp_create(None, 1, 1, 1, 1, C.byref(h)) == echo.ECHO_ERR_ARG
     assert L.echo_decomp_step(None, 1, 1.0, None, None) == echo.ECHO_ERR_ARG
     assert L.echo_decomp_destroy(None) == echo.ECHO_OK
+
+
+@pytest.mark.parametrize("shape", [(2048, 2048, 512), (1 << 20, 1 << 11, 1)])
+def test_create_rejects_grids_of_2_31_cells(shape):
+    """Kernels index cells with 32-bit integers: 2^31 cells and more are refused
+    before any device work."""
+    L = echo.lib()
+    cfg = echo.make_config(*shape)
+    h = C.c_void_p()
+    assert L.echo_create(C.byref(cfg), C.byref(h)) == echo.ECHO_ERR_ARG
+    assert b"2^31" in L.echo_last_error(None)
+
+
+def test_create_accepts_one_cell_per_direction_before_device_check():
+    """A 1 x 1 x 1 grid is a valid configuration: without a GPU the call gets past the
+    argument checks and stops at the device."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = echo.lib()
+    cfg = echo.make_config(1, 1, 1)
+    h = C.c_void_p()
+    assert L.echo_create(C.byref(cfg), C.byref(h)) == echo.ECHO_ERR_CUDA
