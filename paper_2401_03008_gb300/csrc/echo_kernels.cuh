@@ -29,6 +29,55 @@ constexpr int minb_uct(int rbytes) { return rbytes == 4 ? 6 : 3; }
 constexpr int minb_c2p(int rbytes) { return rbytes == 4 ? 4 : 3; }
 constexpr int minb_rk(int rbytes) { return rbytes == 4 ? 6 : 3; }
 
+// Thread-to-cell maps of the sweeps.  T = 0: consecutive cells of the linear
+// order.  T = 1 (2): a block is a 32 x 8 tile of the x-y (x-z) plane, one warp per
+// row of 32 consecutive x; its 8 warps take 8 consecutive y (z) rows, so that a
+// stencil along y (z) re-reads the rows its neighbour warps just loaded, from L1.
+template <int T>
+__device__ __forceinline__ bool tile_cell(const Grid &g, int &i, int &j, int &k)
+{
+    if (T == 0) {
+        const long c = blockIdx.x * (long)BS + threadIdx.x;
+        if (c >= g.n) return false;
+        coords(g, c, i, j, k);
+        return true;
+    }
+    const int nT = T == 1 ? g.ny : g.nz;
+    const unsigned nbx = (unsigned)(g.nx + 31) >> 5, nbt = (unsigned)(nT + 7) >> 3;
+    unsigned b = blockIdx.x;
+    const unsigned bx = b % nbx;
+    b /= nbx;
+    const unsigned bt = b % nbt, bo = b / nbt;
+    i = (int)(32 * bx + (threadIdx.x & 31));
+    const int t = (int)(8 * bt + (threadIdx.x >> 5));
+    if (T == 1) {
+        j = t;
+        k = (int)bo;
+    } else {
+        k = t;
+        j = (int)bo;
+    }
+    return i < g.nx && t < nT;
+}
+
+// blocks of the launch of a kernel with thread map T
+template <int T> inline unsigned tile_blocks(const Grid &g)
+{
+    if (T == 0) return nblocks(g.n, BS);
+    const unsigned nbx = (unsigned)(g.nx + 31) / 32;
+    const unsigned nT = T == 1 ? g.ny : g.nz, no = T == 1 ? g.nz : g.ny;
+    return nbx * ((nT + 7) / 8) * no;
+}
+
+// The map of each sweep (measured on the 256^3 bench): the DER of direction D
+// stacks warps along D and the UCT of edge direction C along its b direction
+// (C + 2) % 3 unless that is x (1-6 % faster each); the flux sweeps, whose many
+// stencil loads per face already overlap within a block, keep the linear order
+// (the tiles made them 2-4 % slower).
+constexpr int flux_map(int) { return 0; }
+constexpr int der_map(int D) { return D; }
+constexpr int uct_map(int C) { return C == 2 ? 1 : 2; }
+
 template <typename R>
 __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
 
@@ -164,16 +213,15 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
     __syncthreads();
     const long n = g.n;
     const int uct = g.uct;
-    long f = blockIdx.x * (long)BS + threadIdx.x;
-    const bool active = f < n;
+    int i, j, k;
+    const bool active = tile_cell<flux_map(D)>(g, i, j, k);
+    const long f = active ? ((long)k * g.ny + j) * g.nx + i : 0;
     R amax = R(0);
     int cs[6];
     R L[8], Rt[8];
     unsigned mask = 0;
     bool own = false;  // face i+1/2 belongs to cell i
     if (active) {
-        int i, j, k;
-        coords(g, f, i, j, k);
         own = owned(g, i, j, k);
         const int iD = D == 0 ? i : (D == 1 ? j : k);
 #pragma unroll
@@ -286,10 +334,9 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
 {
     if (sc->halt) return;
     const long n = g.n;
-    long c = blockIdx.x * (long)BS + threadIdx.x;
-    if (c >= n) return;
     int i, j, k;
-    coords(g, c, i, j, k);
+    if (!tile_cell<der_map(D)>(g, i, j, k)) return;
+    const long c = ((long)k * g.ny + j) * g.nx + i;
     const int iD = D == 0 ? i : (D == 1 ? j : k);
     int fs[6];
 #pragma unroll
@@ -321,8 +368,9 @@ k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__re
     q.reset();
     __syncthreads();
     const long n = g.n;
-    long e = blockIdx.x * (long)BS + threadIdx.x;
-    const bool active = e < n;
+    int i, j, k;
+    const bool active = tile_cell<uct_map(C)>(g, i, j, k);
+    const long e = active ? ((long)k * g.ny + j) * g.nx + i : 0;
     // slots: va[s][t] = 4 s + t, vb[s][t] = 4 s + 2 + t, Ba[t] = 8 + t, Bb[s] = 10 + s
     R r[12];
     unsigned mask = 0;
@@ -339,8 +387,6 @@ k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__re
         }
     };
     if (active) {
-        int i, j, k;
-        coords(g, e, i, j, k);
         const int iA = A == 0 ? i : (A == 1 ? j : k), iB = B == 0 ? i : (B == 1 ? j : k);
 #pragma unroll
         for (int m = 0; m < 6; m++) {
@@ -501,32 +547,39 @@ void Path<R>::int_c2p(echo_ctx *c, int stage, long step, int update_w)
 template <typename R>
 void Path<R>::sweeps(echo_ctx *c, int want_amax)
 {
-    const unsigned nb = nblocks(c->g.n, BS);
+    const Grid &g = c->g;
+    const unsigned nb0 = tile_blocks<flux_map(0)>(g), nb1 = tile_blocks<flux_map(1)>(g),
+                   nb2 = tile_blocks<flux_map(2)>(g);
+    const unsigned nd0 = tile_blocks<der_map(0)>(g), nd1 = tile_blocks<der_map(1)>(g),
+                   nd2 = tile_blocks<der_map(2)>(g);
     const R *prim = (const R *)c->prim;
     const R *bf = face_field<R>(c);
     R *flux = (R *)c->flux, *rhs = (R *)c->rhs;
-    launch(c, K_FLUX_X, k_flux<R, 0>, nb, BS, 0, c->g, prim, bf, flux,
+    launch(c, K_FLUX_X, k_flux<R, 0>, nb0, BS, 0, g, prim, bf, flux,
            (R *)c->fdat[0], c->sc, want_amax);
-    launch(c, K_DER_X, k_der<R, 0>, nb, BS, 0, c->g, (const R *)flux, rhs, 1, c->sc);
-    launch(c, K_FLUX_Y, k_flux<R, 1>, nb, BS, 0, c->g, prim, bf, flux,
+    launch(c, K_DER_X, k_der<R, 0>, nd0, BS, 0, g, (const R *)flux, rhs, 1, c->sc);
+    launch(c, K_FLUX_Y, k_flux<R, 1>, nb1, BS, 0, g, prim, bf, flux,
            (R *)c->fdat[1], c->sc, want_amax);
-    launch(c, K_DER_Y, k_der<R, 1>, nb, BS, 0, c->g, (const R *)flux, rhs, 0, c->sc);
-    launch(c, K_FLUX_Z, k_flux<R, 2>, nb, BS, 0, c->g, prim, bf, flux,
+    launch(c, K_DER_Y, k_der<R, 1>, nd1, BS, 0, g, (const R *)flux, rhs, 0, c->sc);
+    launch(c, K_FLUX_Z, k_flux<R, 2>, nb2, BS, 0, g, prim, bf, flux,
            (R *)c->fdat[2], c->sc, want_amax);
-    launch(c, K_DER_Z, k_der<R, 2>, nb, BS, 0, c->g, (const R *)flux, rhs, 0, c->sc);
+    launch(c, K_DER_Z, k_der<R, 2>, nd2, BS, 0, g, (const R *)flux, rhs, 0, c->sc);
 }
 
 template <typename R>
 void Path<R>::uct(echo_ctx *c)
 {
     if (!c->g.uct) return;
-    const unsigned nb = nblocks(c->g.n, BS);
+    const Grid &g = c->g;
     const R *f0 = (const R *)c->fdat[0], *f1 = (const R *)c->fdat[1], *f2 = (const R *)c->fdat[2];
     const R *bf = face_field<R>(c);
     // E_z from x-faces (a) and y-faces (b); E_x from y and z; E_y from z and x
-    launch(c, K_UCT_Z, k_uct<R, 2>, nb, BS, 0, c->g, bf, f0, f1, (R *)c->E, c->sc);
-    launch(c, K_UCT_X, k_uct<R, 0>, nb, BS, 0, c->g, bf, f1, f2, (R *)c->E, c->sc);
-    launch(c, K_UCT_Y, k_uct<R, 1>, nb, BS, 0, c->g, bf, f2, f0, (R *)c->E, c->sc);
+    launch(c, K_UCT_Z, k_uct<R, 2>, tile_blocks<uct_map(2)>(g), BS, 0, g, bf, f0, f1, (R *)c->E,
+           c->sc);
+    launch(c, K_UCT_X, k_uct<R, 0>, tile_blocks<uct_map(0)>(g), BS, 0, g, bf, f1, f2, (R *)c->E,
+           c->sc);
+    launch(c, K_UCT_Y, k_uct<R, 1>, tile_blocks<uct_map(1)>(g), BS, 0, g, bf, f2, f0, (R *)c->E,
+           c->sc);
 }
 
 template <typename R>
