@@ -62,8 +62,9 @@ enum { ECHO_REC_MP5 = 0, ECHO_REC_LINEAR = 1 };
  * HLL, DER and the UCT fields in single precision; the inversion (Lorentz factor and
  * pressure recovery included) and the Runge-Kutta accumulation of the conserved
  * state in double precision.  The mixed path refines each Newton starting guess
- * with FP32 iterations before the FP64 ones; the FP64 iteration and its stopping
- * rule decide the result. */
+ * with FP32 iterations, then takes FP64 chord steps (FP64 residual, the FP32
+ * slope) and stops after the first undamped one with |dW| <= c2p_tol W, whose
+ * remaining error is below about 1e-5 c2p_tol W. */
 enum { ECHO_FP64 = 0, ECHO_MIXED = 1 };
 /* Newton starting guess: W of the previous call at the same cell, W0 = U, or the
  * small learned network loaded with echo_mlp_load (falls back to the previous W
@@ -82,7 +83,8 @@ typedef struct {
     int rec;            /* ECHO_REC_MP5 or ECHO_REC_LINEAR (also used inside UCT) */
     int precision;      /* ECHO_FP64 or ECHO_MIXED */
     int c2p_guess;      /* ECHO_GUESS_* */
-    double c2p_tol;     /* Newton stop: an undamped step |dW| <= tol W, then one polishing step */
+    double c2p_tol;     /* Newton stop: an undamped step |dW| <= tol W, then one polishing
+                           step (FP64 path; the mixed path stops at that step) */
     int c2p_maxit;      /* Newton iteration cap (a cell past it is a failure) */
     int device;         /* CUDA device ordinal */
     void *stream;       /* cudaStream_t to launch on; NULL: the library makes one */
@@ -115,8 +117,9 @@ echo_status echo_destroy(echo_ctx *ctx);
 echo_status echo_set_state(echo_ctx *ctx, const double *prim, const double *bface,
                            const double *apot, int ptr_kind);
 
-/* Advance by Runge-Kutta steps (SSP-RK3, or SSP-RK2 with rk_order = 2; Sec. 3, steps 1-5) until max_steps steps are done or
- * t reaches t_end (the last step is shortened to land on t_end; pass
+/* Advance by Runge-Kutta steps (SSP-RK3, or SSP-RK2 with rk_order = 2; Sec. 3,
+ * steps 1-5) until max_steps steps are done or t reaches t_end (the last step is
+ * shortened to land on t_end; pass
  * INFINITY for no limit).  *steps_done and *t_now (either may be NULL) receive
  * the steps taken and the time reached.  On ECHO_ERR_C2P or ECHO_ERR_NONFINITE the
  * state, t and the step count are those at the start of the step that failed. */
@@ -193,7 +196,8 @@ echo_status echo_probe_fma_peak(echo_ctx *ctx, int precision, double *flops);
  * W0 = U y.  Parameters: a flat float array of ECHO_MLP_NPARAM values in the order
  * W1[64][5], b1[64], W2[64][64], b2[64], w3[64], b3.  The 64x64 products run as
  * BF16 tensor-core MMAs with FP32 accumulation.  The Newton iteration always runs
- * to tolerance: the guess changes iteration counts, not results. ---- */
+ * to tolerance: the guess changes iteration counts, and results only within that
+ * tolerance. ---- */
 #define ECHO_MLP_NPARAM 4609
 
 typedef struct {
