@@ -188,14 +188,23 @@ __device__ __forceinline__ R minmod4(R a, R b, R c, R d)
 // limiter of Suresh & Huynh (alpha = 4, eps = 1e-10).  Split in two: the smooth
 // candidate with its test, and the limiting that only a few interfaces need.
 template <typename R>
+__device__ __forceinline__ bool mp5_smooth(R um2, R um1, R u0, R up1, R up2, R dp, R &uor)
+{
+    // dp = up1 - u0 (the caller shares it between the two states of a face).  The
+    // test reads (uor - u0)(uor - ump) <= eps with ump = u0 + minmod(dp, alpha (u0 - um1)),
+    // so it needs only d = uor - u0, whose weights are the interpolant's with 1
+    // taken from the centre one (90/128 - 1 = -38/128; all exact binary fractions)
+    const R alpha = R(4);
+    const R d = R(0.0234375) * um2 - R(0.15625) * um1 - R(0.296875) * u0 + R(0.46875) * up1 -
+                R(0.0390625) * up2;
+    uor = u0 + d;
+    return le(d * (d - minmod2(dp, alpha * (u0 - um1))), R(1e-10));
+}
+
+template <typename R>
 __device__ __forceinline__ bool mp5_smooth(R um2, R um1, R u0, R up1, R up2, R &uor)
 {
-    const R alpha = R(4);
-    // the weights over 128 are exact binary fractions: no separate scaling
-    uor = R(0.0234375) * um2 - R(0.15625) * um1 + R(0.703125) * u0 + R(0.46875) * up1 -
-          R(0.0390625) * up2;
-    R ump = u0 + minmod2(up1 - u0, alpha * (u0 - um1));
-    return le((uor - u0) * (uor - ump), R(1e-10));
+    return mp5_smooth(um2, um1, u0, up1, up2, up1 - u0, uor);
 }
 
 template <typename R>
@@ -246,10 +255,11 @@ struct Mp5Queue {
     // The lanes of a warp that need the limiter take consecutive entries with one
     // shared-memory atomic per warp; a warp whose lanes are all smooth skips the
     // queue on a warp-uniform branch.
-    __device__ __forceinline__ R defer(R um2, R um1, R u0, R up1, R up2, int k, unsigned &mask)
+    __device__ __forceinline__ R defer(R um2, R um1, R u0, R up1, R up2, R dp, int k,
+                                       unsigned &mask)
     {
         R uor;
-        const bool smooth = mp5_smooth(um2, um1, u0, up1, up2, uor);
+        const bool smooth = mp5_smooth(um2, um1, u0, up1, up2, dp, uor);
         const unsigned am = __activemask();
         const unsigned need = __ballot_sync(am, !smooth);
         if (need == 0u) return uor;

@@ -240,8 +240,9 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
             } else {
 #pragma unroll
                 for (int m = 0; m < 6; m++) s[m] = ld(pv + cs[m]);
-                L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], 2 * v, mask);
-                Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], 2 * v + 1, mask);
+                const R dc = s[3] - s[2];  // shared by both states of the face
+                L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], dc, 2 * v, mask);
+                Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], -dc, 2 * v + 1, mask);
             }
         }
     }
@@ -382,8 +383,9 @@ k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__re
             r[k] = mc_val(s[1], s[2], s[3]);
             r[k + 1] = mc_val(s[4], s[3], s[2]);
         } else {
-            r[k] = q.defer(s[0], s[1], s[2], s[3], s[4], k, mask);
-            r[k + 1] = q.defer(s[5], s[4], s[3], s[2], s[1], k + 1, mask);
+            const R dc = s[3] - s[2];  // shared by both states
+            r[k] = q.defer(s[0], s[1], s[2], s[3], s[4], dc, k, mask);
+            r[k + 1] = q.defer(s[5], s[4], s[3], s[2], s[1], -dc, k + 1, mask);
         }
     };
     if (active) {
