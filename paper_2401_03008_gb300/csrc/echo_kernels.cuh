@@ -2,7 +2,8 @@
 // (double: FP64 path; float: mixed path).  Included by one translation unit per R.
 //
 // Work split (one thread per output value, x fastest so every stencil load of a
-// warp is a contiguous 32-element row):
+// warp is a contiguous 32-element row; the DER and UCT blocks cover 32 x 8 tiles,
+// see tile_cell):
 //   k_int_c2p   Sec. 3 step 1: INT of the staggered field + Newton inversion.
 //   k_flux<D>   Sec. 3 step 2: MP5 of the 8 primitives at the face above each
 //               cell along D, fluxes, fast speeds, HLL; UCT face data; max speed.
