@@ -171,7 +171,7 @@ def workload_config(args):
                            getattr(args, "rk", 3)),
             "cells": args.n ** 3, "precision": args.precision, "wave": args.wave,
             "l2_flush": "not needed: state of ~%.1f GB >> 129 MB L2" %
-                        (args.n ** 3 * (472 if args.precision == "fp64" else 336) / 1e9),
+                        (args.n ** 3 * (448 if args.precision == "fp64" else 304) / 1e9),
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
