@@ -241,7 +241,7 @@ def main():
 
     n = args.n
     c, st = workload_state(n, args.wave, args.uct)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # the library launches on it; the events are recorded on it
     s = echo.Solver(n, n, n, precision=args.precision, device=local, guess=args.guess,
                     stream=stream.cuda_stream, uct=args.uct, ho=args.ho, rec=args.rec,
                     rk_order=args.rk)
@@ -438,7 +438,7 @@ def run_config(args):
     import torch
     from paper_2401_03008_gb300 import echo
     from paper_2401_03008_gb300 import workloads as wl
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # the library launches on it; the events are recorded on it
     sp = stream.cuda_stream
 
     def timed(sol, steps, t_end=math.inf):

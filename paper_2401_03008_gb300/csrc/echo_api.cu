@@ -112,6 +112,8 @@ void free_all(echo_ctx *c)
                     c->mlp_w, c->guess, c->Bf32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    c->step_graph = nullptr;
     for (auto &r : c->prof) {
         cudaEventDestroy(r.e0);
         cudaEventDestroy(r.e1);
@@ -123,6 +125,13 @@ void free_all(echo_ctx *c)
 }  // namespace
 
 void echo::set_global_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+void echo::drop_step_graph(echo_ctx *c)
+{
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    c->step_graph = nullptr;
+    c->graph_failed = false;
+}
 
 extern "C" {
 
@@ -329,9 +338,9 @@ struct Harvest {
 namespace {
 
 template <typename R>
-void launch_stage(echo_ctx *c, int stage, long idx, Harvest *hv)
+void launch_stage(echo_ctx *c, int stage, Harvest *hv)
 {
-    Path<R>::int_c2p(c, stage, idx, 1);
+    Path<R>::int_c2p(c, stage, 1);
     if (hv) {
         long off = (hv->calls * 7919L) % hv->stride;
         echo::launch_mlp_harvest(c, hv->stride, off, hv->feats, hv->target, hv->capacity,
@@ -342,6 +351,33 @@ void launch_stage(echo_ctx *c, int stage, long idx, Harvest *hv)
     if (stage == 1) echo::launch_dt(c);
     Path<R>::uct(c);
     Path<R>::rk(c, stage);
+}
+
+// Capture one full step on the context's stream into c->step_graph.  A stream that
+// cannot be captured (the legacy default stream, one already capturing) leaves
+// graph_failed set, and the steps are launched directly.
+void build_step_graph(echo_ctx *c)
+{
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->graph_failed = true;
+        return;
+    }
+    const long l0 = c->launches;
+    for (int stage = 1; stage <= c->cfg.rk_order; stage++) {
+        if (c->mixed) launch_stage<float>(c, stage, nullptr);
+        else launch_stage<double>(c, stage, nullptr);
+    }
+    c->graph_kernels = c->launches - l0;
+    c->launches = l0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || !g || cudaGraphInstantiate(&c->step_graph, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        c->step_graph = nullptr;
+        c->graph_failed = true;
+    }
+    if (g) cudaGraphDestroy(g);
 }
 
 echo_status run_steps(echo_ctx *c, int max_steps, double t_end, int *steps_done, double *t_now,
@@ -360,15 +396,27 @@ echo_status run_steps(echo_ctx *c, int max_steps, double t_end, int *steps_done,
     h.fail_step = -1;
     if ((st = write_sc(c, &h))) return st;
     const bool finite_end = isfinite(t_end);
-    for (int s = 0; s < max_steps; s++) {
-        const long idx = step0 + s;
-        for (int stage = 1; stage <= c->cfg.rk_order; stage++) {
-            if (c->mixed) launch_stage<float>(c, stage, idx, hv);
-            else launch_stage<double>(c, stage, idx, hv);
+    // Without a per-step host check (no t_end, no harvest, no per-kernel timing) the
+    // steps are replays of one captured step: a full step's launches as one graph
+    // launch.  Every kernel reads the step state (dt, halt flag, counters) from the
+    // device scalars, so the replays behave exactly like the launches.
+    const bool graph = !finite_end && !hv && !c->prof_on && max_steps >= 2;
+    if (graph && !c->step_graph && !c->graph_failed) build_step_graph(c);
+    if (graph && c->step_graph) {
+        for (int s = 0; s < max_steps; s++) {
+            CK(cudaGraphLaunch(c->step_graph, c->stream));
+            c->launches += c->graph_kernels;
         }
-        if (finite_end) {
-            if ((st = read_sc(c, &h))) return st;
-            if (h.halt) break;
+    } else {
+        for (int s = 0; s < max_steps; s++) {
+            for (int stage = 1; stage <= c->cfg.rk_order; stage++) {
+                if (c->mixed) launch_stage<float>(c, stage, hv);
+                else launch_stage<double>(c, stage, hv);
+            }
+            if (finite_end) {
+                if ((st = read_sc(c, &h))) return st;
+                if (h.halt) break;
+            }
         }
     }
     if ((st = sync_check(c))) return st;
@@ -458,7 +506,7 @@ echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *am
         }
     }
     if (c->mixed) {
-        Path<float>::int_c2p(c, 0, -1, 1);
+        Path<float>::int_c2p(c, 0, 1);
         Path<float>::sweeps(c, 1);
         Path<float>::uct(c);
         if (c->g.uct) {
@@ -468,7 +516,7 @@ echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *am
             Path<float>::rhs_out(c, tmp8);
         }
     } else {
-        Path<double>::int_c2p(c, 0, -1, 1);
+        Path<double>::int_c2p(c, 0, 1);
         Path<double>::sweeps(c, 1);
         Path<double>::uct(c);
         if (c->g.uct) {

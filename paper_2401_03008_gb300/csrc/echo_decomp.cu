@@ -227,11 +227,11 @@ void free_decomp(echo_decomp *d)
 }
 
 template <typename R>
-void substep(echo_decomp *d, int stage, long idx)
+void substep(echo_decomp *d, int stage)
 {
     exchange(d);
     for (echo_ctx *c : d->sub) {
-        echo::Path<R>::int_c2p(c, stage, idx, 1);
+        echo::Path<R>::int_c2p(c, stage, 1);
         echo::Path<R>::sweeps(c, stage == 1);
     }
     if (stage == 1) echo::launch_dt(d->sub[0]);
@@ -432,8 +432,8 @@ echo_status echo_decomp_step(echo_decomp *d, int max_steps, double t_end, int *s
     const bool finite_end = std::isfinite(t_end);
     for (int s = 0; s < max_steps; s++) {
         for (int stage = 1; stage <= d->cfg.rk_order; stage++) {
-            if (mixed) substep<float>(d, stage, step0 + s);
-            else substep<double>(d, stage, step0 + s);
+            if (mixed) substep<float>(d, stage);
+            else substep<double>(d, stage);
         }
         if (finite_end) {
             if ((st = read_sc(d, &h))) return st;

@@ -49,6 +49,12 @@ struct echo_ctx {
     bool has_state;
     long launches;
     bool prof_on;
+    // one full step captured as a CUDA graph and replayed for runs without a
+    // per-step host check (see run_steps); rebuilt when the launch set changes
+    cudaGraphExec_t step_graph;
+    long graph_kernels;     // kernels in one replay (for the launch count)
+    bool graph_failed;      // capture not possible on this stream: launch directly
+    unsigned mlp_blocks;    // persistent grid of the learned-guess kernel (0: not loaded)
     std::vector<echo::ProfRec> prof;
     long prof_count[ECHO_NKERNELS];
     double prof_ms[ECHO_NKERNELS];
@@ -91,7 +97,7 @@ struct Path {
     // (learned guesses when selected and loaded, then) INT + C2P into the work prims
     // (R).  stage: 1..3 (0 for a one-off call); update_w: store the converged W as
     // the next warm guess.
-    static void int_c2p(echo_ctx *c, int stage, long step, int update_w);
+    static void int_c2p(echo_ctx *c, int stage, int update_w);
     // sweeps + DER (steps 2-3), want_amax on the first stage of a step
     static void sweeps(echo_ctx *c, int want_amax);
     // UCT edge fields (step 4, first half)
@@ -102,6 +108,8 @@ struct Path {
     static void curl_out(echo_ctx *c, double *out);
     // copy the work rhs (R) to a double array
     static void rhs_out(echo_ctx *c, double *out);
+    // blocks of the persistent learned-guess kernel that fit on the device at once
+    static unsigned mlp_grid(echo_ctx *c);
 };
 
 // precision-independent launchers (FP64 translation unit)
@@ -119,6 +127,8 @@ void launch_bf32(echo_ctx *c);
 double probe_fma_peak(echo_ctx *c, int fp64);
 // error text of calls without a context (returned by echo_last_error(NULL))
 void set_global_error(const char *msg);
+// drop the captured step graph (the launch set changed)
+void drop_step_graph(echo_ctx *c);
 // harvest of training states (features, converged W/U)
 void launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,
                         long capacity, unsigned long long *count);

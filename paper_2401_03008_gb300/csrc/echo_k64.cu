@@ -69,7 +69,7 @@ void launch_prims_out(echo_ctx *c, double *out8)
 {
     C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, ECHO_GUESS_PREV, 0};
     launch(c, K_C2P, k_int_c2p<double>, nblocks(c->g.n, BS), BS, 0, c->g, (const double *)c->U,
-           (const double *)c->Bf, c->W, (const float *)nullptr, out8, par, c->sc, 0, -1L, 0, 0);
+           (const double *)c->Bf, c->W, (const float *)nullptr, out8, par, c->sc, 0, 0, 0);
 }
 
 __global__ void __launch_bounds__(BS)

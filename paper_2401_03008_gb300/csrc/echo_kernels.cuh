@@ -92,7 +92,7 @@ template <typename R>
 __global__ void __launch_bounds__(BS, minb_c2p(sizeof(R)))
 k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
           double *__restrict__ W, const float *__restrict__ guess, R *__restrict__ prim,
-          C2PParams par, DevScalars *sc, int stage, long step, int update_w, int count)
+          C2PParams par, DevScalars *sc, int stage, int update_w, int count)
 {
     // the flag is set by other blocks of this launch: read it once per warp so that
     // the warp-wide reductions below always see all 32 lanes
@@ -159,7 +159,8 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
         if (nf) atomicAdd(&sc->fallbacks, nf);
         if (nb) {
             atomicAdd(&sc->fails, nb);
-            if (atomicCAS(&sc->fail_stage, 0, stage) == 0) sc->fail_step = step;
+            // the step in progress is the count of completed ones
+            if (atomicCAS(&sc->fail_stage, 0, stage) == 0) sc->fail_step = (long)sc->step;
             atomicOr(&sc->halt, 1);
         }
     }
@@ -525,26 +526,32 @@ template <> inline const double *face_field<double>(echo_ctx *c) { return c->Bf;
 template <> inline const float *face_field<float>(echo_ctx *c) { return c->Bf32; }
 
 template <typename R>
-void Path<R>::int_c2p(echo_ctx *c, int stage, long step, int update_w)
+void Path<R>::int_c2p(echo_ctx *c, int stage, int update_w)
 {
     // the mixed path refines the guess with FP32 Newton iterations first
     C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, c->cfg.c2p_guess, c->mixed ? 1 : 0};
     const bool mlp = par.guess == ECHO_GUESS_MLP && c->mlp_w && c->guess;
     if (par.guess == ECHO_GUESS_MLP && !mlp) par.guess = ECHO_GUESS_PREV;
     if (mlp) {
-        // persistent grid: as many blocks as can be resident at once
-        int nsm = 152, per_sm = 1;
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->cfg.device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_guess<R>, MLP_BS, 0);
+        // persistent grid: as many blocks as can be resident at once (sized when the
+        // weights were loaded, outside any stream capture)
         unsigned nb = nblocks(c->g.n, MLP_BS);
-        const unsigned cap = (unsigned)(nsm * (per_sm > 0 ? per_sm : 1));
-        if (nb > cap) nb = cap;
+        if (c->mlp_blocks && nb > c->mlp_blocks) nb = c->mlp_blocks;
         launch(c, K_MLP, k_mlp_guess<R>, nb, MLP_BS, 0, c->g, (const double *)c->U,
                face_field<R>(c), (const MlpDev *)c->mlp_w, c->guess);
     }
     launch(c, K_C2P, k_int_c2p<R>, nblocks(c->g.n, BS), BS, 0, c->g, (const double *)c->U,
            (const double *)c->Bf, c->W, mlp ? (const float *)c->guess : (const float *)nullptr,
-           (R *)c->prim, par, c->sc, stage, step, update_w, 1);
+           (R *)c->prim, par, c->sc, stage, update_w, 1);
+}
+
+template <typename R>
+unsigned Path<R>::mlp_grid(echo_ctx *c)
+{
+    int nsm = 152, per_sm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->cfg.device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_guess<R>, MLP_BS, 0);
+    return (unsigned)(nsm * (per_sm > 0 ? per_sm : 1));
 }
 
 template <typename R>

@@ -380,6 +380,10 @@ echo_status echo_mlp_load(echo_ctx *c, const float *weights, long n)
     c->launches++;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     cudaFree(dp);
+    // the persistent grid of the guess kernel, and a step graph without that kernel
+    // no longer matches the launches
+    c->mlp_blocks = c->mixed ? echo::Path<float>::mlp_grid(c) : echo::Path<double>::mlp_grid(c);
+    echo::drop_step_graph(c);
     return e == cudaSuccess ? ECHO_OK : ECHO_ERR_CUDA;
 }
 
