@@ -122,7 +122,11 @@ echo_status echo_set_state(echo_ctx *ctx, const double *prim, const double *bfac
  * shortened to land on t_end; pass
  * INFINITY for no limit).  *steps_done and *t_now (either may be NULL) receive
  * the steps taken and the time reached.  On ECHO_ERR_C2P or ECHO_ERR_NONFINITE the
- * state, t and the step count are those at the start of the step that failed. */
+ * state, t and the step count are those at the start of the step that failed.
+ * Without t_end (and without kernel timing) the first call captures one full step
+ * as a CUDA graph on the context's stream and every step replays it.  The call
+ * synchronises its stream before returning, so it cannot itself be captured into a
+ * caller's graph. */
 echo_status echo_step(echo_ctx *ctx, int max_steps, double t_end, int *steps_done,
                       double *t_now);
 
