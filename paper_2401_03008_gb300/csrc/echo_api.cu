@@ -287,6 +287,7 @@ echo_status echo_destroy(echo_ctx *c)
 echo_status echo_set_state(echo_ctx *c, const double *prim, const double *bface,
                            const double *apot, int ptr_kind)
 {
+    echo::Range r("echo_set_state");
     if (!c) return fail(nullptr, ECHO_ERR_ARG, "ctx is NULL");
     if (!prim) return fail(c, ECHO_ERR_ARG, "prim is NULL");
     echo_status st = select_device(c);
@@ -340,6 +341,8 @@ namespace {
 template <typename R>
 void launch_stage(echo_ctx *c, int stage, Harvest *hv)
 {
+    static const char *names[4] = {"stage", "stage 1", "stage 2", "stage 3"};
+    echo::Range r(names[stage < 4 ? stage : 0]);
     Path<R>::int_c2p(c, stage, 1);
     if (hv) {
         long off = (hv->calls * 7919L) % hv->stride;
@@ -446,6 +449,7 @@ extern "C" {
 
 echo_status echo_step(echo_ctx *c, int max_steps, double t_end, int *steps_done, double *t_now)
 {
+    echo::Range r("echo_step");
     if (!c) return fail(nullptr, ECHO_ERR_ARG, "ctx is NULL");
     return run_steps(c, max_steps, t_end, steps_done, t_now, nullptr);
 }
@@ -608,6 +612,7 @@ echo_status echo_set_conserved(echo_ctx *c, const double *cons5, const double *b
 
 echo_status echo_diagnostics(echo_ctx *c, echo_diag *out, int reset_counters)
 {
+    echo::Range r("echo_diagnostics");
     if (!c || !out) return fail(c, ECHO_ERR_ARG, "ctx or out is NULL");
     if (!c->has_state) return fail(c, ECHO_ERR_STATE, "no state");
     echo_status st = select_device(c);

@@ -195,6 +195,7 @@ echo_status write_sc(echo_decomp *d, const DevScalars *h)
 
 void exchange(echo_decomp *d)
 {
+    echo::Range r("halo exchange");
     dim3 grid(nblocks(d->gm.npadc, BS), d->nsub);
     k_exchange<<<grid, BS, 0, d->stream>>>(d->gm, d->dsub);
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -84,6 +85,16 @@ inline void launch(echo_ctx *c, int kind, Kernel k, dim3 grid, dim3 block, size_
 }
 
 inline unsigned nblocks(long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// NVTX range for the host phases (a step, a stage, set-up, diagnostics, the halo
+// exchange): a profiler attached to the process shows them on its timeline; without
+// one the calls return at once.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // Number of blocks of the fixed-shape reductions (a multiple of the SM count of
 // the GB300, 152, so the partial sums have a fixed order).
