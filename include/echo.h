@@ -31,9 +31,9 @@
  *   - Every call returns an echo_status.  Nothing aborts, traps or prints.  The
  *     text of the last error of a context is available from echo_last_error().
  *   - A context is used by one host thread at a time.  All state lives in the
- *     context, except the text of the last error of a call made without one (one
- *     static buffer per library, see echo_last_error(NULL)) and the fixed scratch
- *     array of echo_diagnostics_noalloc.
+ *     context, except the text of the last error of a call made without one
+ *     (static buffers: echo_last_error(NULL), echo_decomp_last_error(NULL)) and the
+ *     fixed scratch array of echo_diagnostics_noalloc.
  */
 #ifndef ECHO_H
 #define ECHO_H
