@@ -12,6 +12,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -110,6 +111,20 @@ def dist_setup(args):
     return world, rank, local
 
 
+def _cpu_model():
+    """the host CPU's model name and core count (for the oracle timings)"""
+    name = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "%s, %d cores" % (name, os.cpu_count() or 1)
+
+
 def job_rate(ms, units_per_rank, world, device="cuda"):
     """The slowest rank's timed milliseconds (max over the process group) and the
     whole-job rate: the units all ranks processed over that time.  Replicas share
@@ -186,7 +201,8 @@ def cpu_baseline(args):
     g.step(steps)
     el = time.perf_counter() - t0
     return {"value": ns ** 3 * steps / el, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": "%d^3 grid of the same wave, %d SSP-RK3 steps, %.1f s" % (ns, steps, el)}
+            "sample": "%d^3 grid of the same wave, %d SSP-RK3 steps, %.1f s on %s"
+                      % (ns, steps, el, _cpu_model())}
 
 
 def main():
@@ -204,8 +220,8 @@ def main():
     ap.add_argument("--rec", default="mp5", choices=["mp5", "linear"])
     ap.add_argument("--rk", type=int, default=3, choices=[2, 3])
     ap.add_argument("--ref-n", type=int, default=48)
-    ap.add_argument("--cpu-n", type=int, default=64)
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-n", type=int, default=128)   # about 10 s of oracle work
+    ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -469,6 +485,12 @@ def run_config(args):
         t0 = time.perf_counter()
         g.step(20)
         el = time.perf_counter() - t0
+        # the oracle on one core as well (the same 20 steps)
+        g1 = orc.Grid(n, n, n, nthreads=1)
+        g1.set_state(*st)
+        t0 = time.perf_counter()
+        g1.step(20)
+        el1 = time.perf_counter() - t0
         p, ref = s.primitives(), g.primitives()
         rel = []
         for grp in ([0], [1, 2, 3], [4], [5, 6, 7]):
@@ -477,6 +499,8 @@ def run_config(args):
         out.update({"workload": "Alfven wave along x, 32^3, FP64, 20 steps", "steps": done,
                     "t": t, "gpu_cell_updates_per_s": n ** 3 * 20 / (ms * 1e-3),
                     "oracle_cell_updates_per_s": n ** 3 * 20 / el, "oracle_threads": os.cpu_count(),
+                    "oracle_one_core_cell_updates_per_s": n ** 3 * 20 / el1,
+                    "host_cpu": _cpu_model(),
                     "max_rel_diff_vs_oracle": rel,
                     "l1_vs_exact": list(map(float, s.l1_error(c.exact_prim8(t))))})
     elif args.config in (2, 3):
