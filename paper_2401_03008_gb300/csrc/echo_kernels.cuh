@@ -34,10 +34,17 @@ constexpr int minb_rk(int rbytes) { return rbytes == 4 ? 6 : 3; }
 // order.  T = 1 (2): a block is a 32 x 8 tile of the x-y (x-z) plane, one warp per
 // row of 32 consecutive x; its 8 warps take 8 consecutive y (z) rows, so that a
 // stencil along y (z) re-reads the rows its neighbour warps just loaded, from L1.
+// A grid with fewer than 8 cells along the stacking direction (a 2-D grid, a thin
+// block) would leave most warps of a tile idle: it takes the linear order.
+template <int T> __host__ __device__ __forceinline__ bool tiled(const Grid &g)
+{
+    return T != 0 && (T == 1 ? g.ny : g.nz) >= 8;
+}
+
 template <int T>
 __device__ __forceinline__ bool tile_cell(const Grid &g, int &i, int &j, int &k)
 {
-    if (T == 0) {
+    if (!tiled<T>(g)) {
         const long c = blockIdx.x * (long)BS + threadIdx.x;
         if (c >= g.n) return false;
         coords(g, c, i, j, k);
@@ -64,7 +71,7 @@ __device__ __forceinline__ bool tile_cell(const Grid &g, int &i, int &j, int &k)
 // blocks of the launch of a kernel with thread map T
 template <int T> inline unsigned tile_blocks(const Grid &g)
 {
-    if (T == 0) return nblocks(g.n, BS);
+    if (!tiled<T>(g)) return nblocks(g.n, BS);
     const unsigned nbx = (unsigned)(g.nx + 31) / 32;
     const unsigned nT = T == 1 ? g.ny : g.nz, no = T == 1 ? g.nz : g.ny;
     return nbx * ((nT + 7) / 8) * no;
