@@ -224,6 +224,10 @@ class Solver:
 
     # ------------------------------------------------------------------
     def set_state(self, prim, bface=None, apot=None):
+        """Initial data (echo_set_state): prim [5][nz][ny][nx] = rho, v, p at cell
+        centres; bface [3][nz][ny][nx] the face field (cell-centred with uct=0);
+        apot [3][nz][ny][nx] an edge vector potential whose curl is added.  numpy
+        arrays (host) or float64 CUDA tensors (device), all of one kind."""
         n = self.n
         p, kp = _ptr(prim, "prim", 5 * n)
         b, kb = _ptr(bface, "bface", 3 * n)
@@ -233,6 +237,9 @@ class Solver:
         self._check(self.L.echo_set_state(self._h, p, b, a, kind))
 
     def step(self, max_steps=1, t_end=math.inf):
+        """Advance up to max_steps Runge-Kutta steps, the last one shortened to land on
+        t_end (echo_step); returns (steps taken, time reached).  Raises EchoError
+        (status ECHO_ERR_C2P) after rolling back a step whose inversion failed."""
         done = C.c_int()
         t = C.c_double()
         st = self.L.echo_step(self._h, max_steps, t_end, C.byref(done), C.byref(t))
@@ -246,6 +253,8 @@ class Solver:
         return np.empty(shape, dtype=np.float64)
 
     def rhs(self, device=False):
+        """One evaluation of the right-hand side (echo_rhs): (d/dt of the 5 conserved
+        cell variables, d/dt of the 3 face-field arrays, largest HLL speed)."""
         n = self.n
         rc = self._out(5 * n, (5,) + self.shape, device)
         rb = self._out(3 * n, (3,) + self.shape, device)
@@ -257,6 +266,8 @@ class Solver:
         return rc, rb, amax.value
 
     def primitives(self, out=None, device=False):
+        """[8][nz][ny][nx] = rho, vx, vy, vz, p, Bx, By, Bz with the field at cell
+        centres (echo_get_primitives); into out if given (numpy or CUDA tensor)."""
         if out is None:
             out = self._out(8 * self.n, (8,) + self.shape, device)
         p, kind = _ptr(out, "out", 8 * self.n)
@@ -265,6 +276,8 @@ class Solver:
         return out
 
     def get_state(self, cons=None, bface=None, w=None, device=False):
+        """Checkpoint (echo_get_state): (cons [5][...], bface [3][...], Newton guess
+        W [...], t, step)."""
         n = self.n
         cons = self._out(5 * n, (5,) + self.shape, device) if cons is None else cons
         bface = self._out(3 * n, (3,) + self.shape, device) if bface is None else bface
@@ -279,6 +292,8 @@ class Solver:
         return cons, bface, w, t.value, step.value
 
     def set_conserved(self, cons, bface, w=None, t=0.0, step=0):
+        """Resume from a checkpoint of get_state (echo_set_conserved); bit-identical
+        to an uninterrupted run."""
         n = self.n
         pc, kc = _ptr(cons, "cons", 5 * n)
         pb, kb = _ptr(bface, "bface", 3 * n)
@@ -288,11 +303,14 @@ class Solver:
         self._check(self.L.echo_set_conserved(self._h, pc, pb, pw, t, step, kind))
 
     def diagnostics(self, reset=False):
+        """Totals, div B, Newton statistics of the current state (echo_diagnostics) as
+        a dict; reset=True clears the Newton counters afterwards."""
         d = Diag()
         self._check(self.L.echo_diagnostics(self._h, C.byref(d), int(reset)))
         return d.as_dict()
 
     def l1_error(self, ref):
+        """Mean |primitives - ref| per variable (echo_l1_error), ref [8][nz][ny][nx]."""
         p, kind = _ptr(ref, "ref", 8 * self.n)
         out = (C.c_double * 8)()
         self._sync_torch(kind)
@@ -361,6 +379,10 @@ class Decomp:
             pass
 
     def set_state(self, prim, bface=None, apot=None):
+        """Initial data (echo_set_state): prim [5][nz][ny][nx] = rho, v, p at cell
+        centres; bface [3][nz][ny][nx] the face field (cell-centred with uct=0);
+        apot [3][nz][ny][nx] an edge vector potential whose curl is added.  numpy
+        arrays (host) or float64 CUDA tensors (device), all of one kind."""
         n = self.n
         p, kp = _ptr(prim, "prim", 5 * n)
         b, kb = _ptr(bface, "bface", 3 * n)
