@@ -122,3 +122,21 @@ def test_create_accepts_one_cell_per_direction_before_device_check():
     cfg = echo.make_config(1, 1, 1)
     h = C.c_void_p()
     assert L.echo_create(C.byref(cfg), C.byref(h)) == echo.ECHO_ERR_CUDA
+
+
+def test_binding_marshals_only_float64_arrays_of_the_right_size():
+    """The binding passes numpy arrays as host pointers and CUDA tensors as device
+    pointers; anything else is refused before the library is called."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    p, kind = echo._ptr(np.zeros(10), "x", 10)
+    assert kind == echo.PTR_HOST and p.value
+    assert echo._ptr(None, "x", 10) == (None, None)
+    for bad in (np.zeros(10, dtype=np.float32), np.zeros((4, 5))[:, ::2], np.zeros(9),
+                torch.zeros(10, dtype=torch.float64), [0.0] * 10):
+        with pytest.raises(ValueError):
+            echo._ptr(bad, "x", 10)
+    with pytest.raises(ValueError):
+        echo.Solver._same_kind(echo.PTR_HOST, echo.PTR_DEVICE)
+    assert echo.Solver._same_kind(None, echo.PTR_DEVICE, None) == echo.PTR_DEVICE
+    assert echo.Solver._same_kind(None, None) == echo.PTR_HOST
