@@ -1,12 +1,18 @@
 """Benchmark: cell-updates per second of the SSP-RK3 step on one GB300.
 
-Workload (default): the circularly polarised relativistic Alfven wave with k along
-(1,1,1) on a periodic 256^3 grid, FP64, UCT and high-order INT/DER on, MP5,
+Workload (default): decaying relativistic Alfvenic turbulence on a periodic 768^3
+grid of a (2 pi)^3 box -- rho0 = 1, B0 along z with sigma0 = B0^2/rho0 = 10,
+beta0 = 1, random-phase modes with 1 <= |k| <= 4, mean |dB|/B0 = 0.5, largest
+Lorentz factor 5, seeded -- with UCT and high-order INT/DER on, MP5, SSP-RK3 and
 CFL 0.4.  One "step" is one full SSP-RK3 step (three substeps of the whole
-right-hand side) over all cells; value = cells * steps / time.
+right-hand side) over all cells; value = cells * steps / time of the FP64 path.
+The same line carries the mixed path and the mixed path with the learned Newton
+guess on the same workload and step count (rate, Newton iterations, fallback
+rate, L1 distance to the FP64 state), the end-to-end rate through the C ABI with
+host buffers, the roofline of the dominant kernel and the oracle on the host.
 
-The state (about 8 GB) is far larger than the 129 MB L2, so no flush is needed
-between timed steps.  Prints one JSON line.
+The state (about 200 GB in FP64) is far larger than the 129 MB L2, so no flush is
+needed between timed steps.  Prints one JSON line.
 """
 import argparse
 import json
@@ -22,8 +28,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "cell-updates/s per GB300 (SSP-RK3 step, FP64)"
+METRIC = ("cell-updates/s per GB300 (FP64 vs mixed+learned C2P) at stated L1 error; "
+          "% HBM peak")
 UNIT = "cell-updates/s"
+SEED = 2401_03008
 
 # Algorithmic per-unit costs of each kernel kind: one unit is one cell, face or edge
 # of the launch.  Bytes: each array element read or written once (stencil
@@ -139,6 +147,7 @@ def job_rate(ms, units_per_rank, world, device="cuda"):
 
 
 def workload_state(n, wave, uct=1):
+    """The Alfven-wave workloads (host arrays): (wave, (prim5, bface, apot))."""
     from paper_2401_03008_gb300 import workloads as wl
     m = {"oblique": (1, 1, 1), "x": (1, 0, 0)}[wave]
     c = wl.CPA(n, n, n, m=m)
@@ -147,28 +156,94 @@ def workload_state(n, wave, uct=1):
     return c, (c.prim5(), c.bface_background(), c.apot())
 
 
+def turbulence_state(n, lorentz_max, seed=SEED, device=None):
+    """The decaying-turbulence workload on an n^3 grid: (prim5, bface, apot), numpy
+    arrays, or float64 tensors generated on ``device`` (the 768^3 synthesis would
+    take minutes on the host)."""
+    from paper_2401_03008_gb300 import workloads as wl
+    tb = wl.Turbulence(n, seed=seed, lorentz_max=lorentz_max, device=device)
+    st = (tb.prim5(), tb.bface_background(), tb.apot())
+    tb.release()
+    return st
+
+
+TURB_L = (2 * math.pi,) * 3
+
+
+def state_for(args, n, device=None):
+    """(box, (prim5, bface, apot)) of the selected workload on an n^3 grid."""
+    if args.workload == "turbulence":
+        return TURB_L, turbulence_state(n, args.lorentz_max, device=device)
+    _, st = workload_state(n, args.wave, args.uct)
+    return (1.0, 1.0, 1.0), st
+
+
+def workload_name(args, n):
+    if args.workload == "turbulence":
+        return ("decaying relativistic Alfvenic turbulence, %d^3 periodic (2 pi)^3 box, "
+                "sigma0 = 10, beta0 = 1, mean |dB|/B0 = 0.5, max Lorentz factor %g, "
+                "1 <= |k| <= 4, seed %d; UCT on, HO on, MP5, CFL 0.4, SSP-RK3"
+                % (n, args.lorentz_max, SEED))
+    return ("relativistic circularly polarised Alfven wave, k along %s, %d^3 periodic, "
+            "UCT %s, HO %s, %s, CFL 0.4, SSP-RK%d"
+            % ({"oblique": "(1,1,1)", "x": "x"}[args.wave], n,
+               "on" if args.uct else "off", "on" if args.ho else "off",
+               "MP5" if args.rec == "mp5" else "linear (MC)", args.rk))
+
+
+def workload_config(args):
+    bpc = 448 if args.precision == "fp64" else 304
+    return {"workload": workload_name(args, args.n), "cells": args.n ** 3,
+            "precision": args.precision,
+            "l2_flush": "not needed: state of ~%.0f GB >> 129 MB L2" % (args.n ** 3 * bpc / 1e9),
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def _oracle_sample(args, ns):
+    """An oracle grid with the ns^3 sample of the workload."""
+    from oracle import oracle as orc
+    L, st = state_for(args, ns)
+    g = orc.Grid(ns, ns, ns, *L, nthreads=os.cpu_count() or 1, uct=args.uct, ho=args.ho,
+                 rec=1 if args.rec == "linear" else 0, rk=args.rk)
+    g.set_state(*st)
+    return g, st
+
+
+def _oracle_steps_from_start(args, ns, steps):
+    """Seconds of oracle work for `steps` SSP-RK3 steps of the ns^3 sample, each taken
+    from the sample's initial state (the reset is outside the timed region), so every
+    timed step is the same bounded piece of the workload."""
+    g, st = _oracle_sample(args, ns)
+    el = 0.0
+    for _ in range(steps):
+        g.set_state(*st)
+        t0 = time.perf_counter()
+        bad = g.step(1)
+        el += time.perf_counter() - t0
+        if bad:
+            raise RuntimeError("the oracle's inversion failed on the %d^3 sample (too coarse "
+                               "for this workload); choose a larger sample" % ns)
+    return el
+
+
 def run_reference(args, world, rank):
     """The oracle (plain FP64 C, all host cores) on a bounded sample of the same
-    workload: the same wave on a smaller grid, one SSP-RK3 step per timed step."""
+    workload: one SSP-RK3 step of the --ref-n^3 grid per timed step."""
     if rank != 0:
         return
-    from oracle import oracle as orc
     nthreads = os.cpu_count() or 1
     ns = args.ref_n
-    c, st = workload_state(ns, args.wave)
-    g = orc.Grid(ns, ns, ns, nthreads=nthreads)
-    g.set_state(*st)
-    g.step(args.warmup)
-    t0 = time.perf_counter()
-    g.step(args.steps)
-    el = time.perf_counter() - t0
+    _oracle_steps_from_start(args, ns, args.warmup)
+    el = _oracle_steps_from_start(args, ns, args.steps)
     value = ns ** 3 * args.steps / el
-    sample = "%d^3 grid, same wave, %d SSP-RK3 steps (oracle)" % (ns, args.steps)
+    sample = ("%d^3 grid of the same workload, %d SSP-RK3 steps, each from its initial "
+              "state (oracle, %s)" % (ns, args.steps, _cpu_model()))
+    cfg = workload_config(args)
+    cfg.update({"sample": sample, "cells": ns ** 3})
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(args),
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -176,33 +251,13 @@ def run_reference(args, world, rank):
     print(json.dumps(out))
 
 
-def workload_config(args):
-    return {"workload": "relativistic circularly polarised Alfven wave, k along %s, "
-                        "%d^3 periodic, UCT %s, HO %s, %s, CFL 0.4, SSP-RK%d"
-                        % ({"oblique": "(1,1,1)", "x": "x"}[args.wave], args.n,
-                           "on" if getattr(args, "uct", 1) else "off",
-                           "on" if getattr(args, "ho", 1) else "off",
-                           "MP5" if getattr(args, "rec", "mp5") == "mp5" else "linear (MC)",
-                           getattr(args, "rk", 3)),
-            "cells": args.n ** 3, "precision": args.precision, "wave": args.wave,
-            "l2_flush": "not needed: state of ~%.1f GB >> 129 MB L2" %
-                        (args.n ** 3 * (448 if args.precision == "fp64" else 304) / 1e9),
-            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
-
-
 def cpu_baseline(args):
-    from oracle import oracle as orc
     nthreads = os.cpu_count() or 1
     ns, steps = args.cpu_n, args.cpu_steps
-    c, st = workload_state(ns, args.wave)
-    g = orc.Grid(ns, ns, ns, nthreads=nthreads)
-    g.set_state(*st)
-    t0 = time.perf_counter()
-    g.step(steps)
-    el = time.perf_counter() - t0
+    el = _oracle_steps_from_start(args, ns, steps)
     return {"value": ns ** 3 * steps / el, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": "%d^3 grid of the same wave, %d SSP-RK3 steps, %.1f s on %s"
-                      % (ns, steps, el, _cpu_model())}
+            "sample": "%d^3 grid of the same workload, %d SSP-RK3 steps each from its initial "
+                      "state, %.1f s on %s" % (ns, steps, el, _cpu_model())}
 
 
 def main():
@@ -211,7 +266,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--workload", default="turbulence", choices=["turbulence", "wave"])
+    ap.add_argument("--n", type=int, default=768)
+    ap.add_argument("--lorentz-max", type=float, default=5.0)
     ap.add_argument("--wave", default="oblique", choices=["oblique", "x"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--guess", default="prev", choices=["prev", "cold", "mlp"])
@@ -219,13 +276,15 @@ def main():
     ap.add_argument("--ho", type=int, default=1, help="0: two-point INT and DER")
     ap.add_argument("--rec", default="mp5", choices=["mp5", "linear"])
     ap.add_argument("--rk", type=int, default=3, choices=[2, 3])
-    ap.add_argument("--ref-n", type=int, default=48)
+    ap.add_argument("--ref-n", type=int, default=64)
     ap.add_argument("--cpu-n", type=int, default=128)   # about 10 s of oracle work
-    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", type=int, default=1, help="also time mixed and mixed+learned")
+    ap.add_argument("--train-n", type=int, default=128)
+    ap.add_argument("--train-steps", type=int, default=20)
     ap.add_argument("--config", type=int, default=0,
                     help="1..5: benchmark-plan configurations; 6: the 2.5-D turbulence run of "
                          "Sec. 5; 7: 2 x 2 x 2 blocks with the wide halo against one grid")
@@ -236,6 +295,8 @@ def main():
     ap.add_argument("--config6-t", type=float, default=20.0)
     ap.add_argument("--config6-out", default="", help="write the spectra (.npz) here")
     args = ap.parse_args()
+    if args.workload == "turbulence":
+        args.uct, args.ho, args.rec, args.rk = 1, 1, "mp5", 3
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
@@ -256,16 +317,19 @@ def main():
             dist.barrier()
 
     n = args.n
-    c, st = workload_state(n, args.wave, args.uct)
+    dev = "cuda:%d" % local
     stream = torch.cuda.Stream()  # the library launches on it; the events are recorded on it
-    s = echo.Solver(n, n, n, precision=args.precision, device=local, guess=args.guess,
+    L, st = state_for(args, n, device=dev)
+    s = echo.Solver(n, n, n, L=L, precision=args.precision, device=local, guess=args.guess,
                     stream=stream.cuda_stream, uct=args.uct, ho=args.ho, rec=args.rec,
                     rk_order=args.rk)
+    weights, train_info = None, None
     if args.guess == "mlp":
-        mk = lambda m: workload_state(m, args.wave)[1]
-        w, _ = harvest_and_train(64, 8, 4, mk, (1.0, 1.0, 1.0), 2401030081)
-        s.mlp_load(w)
+        weights, train_info = train_guess(args)
+        s.mlp_load(weights)
     s.set_state(*st)
+    del st
+    torch.cuda.empty_cache()
     s.step(args.warmup)
     torch.cuda.synchronize()
     barrier()
@@ -287,30 +351,37 @@ def main():
     assert done == args.steps
     ms, value = job_rate(ms, n ** 3 * args.steps, world)
     diag = s.diagnostics()
-    # FP64 state after warm-up + timed steps: the variants are compared with it
-    ref = s.primitives() if (args.variants and args.precision == "fp64" and args.uct
-                             and args.ho and args.rec == "mp5" and args.rk == 3) else None
+    # the state after warm-up + timed steps: the variants are compared with it
+    ref = s.primitives(device=True) if args.variants else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-           "data": "synthetic (analytic Alfven wave)", "config": workload_config(args),
+           "data": ("synthetic (seeded random-phase turbulence, generated on the GPU)"
+                    if args.workload == "turbulence" else "synthetic (analytic Alfven wave)"),
+           "config": workload_config(args),
            "gpu_launches": launches, "clocks": clocks,
            "diag": {"t": diag["t"], "divb_max": diag["divb_max"],
                     "newton_it_mean": diag["newton_it_mean"],
+                    "c2p_fallbacks": diag["c2p_fallbacks"],
                     "c2p_failures": diag["c2p_failures"]}}
+    if train_info:
+        out["training"] = train_info
     if args.prof_steps > 0:
         out.update(roofline_and_profile(args, s, n))
-    if ref is not None:
-        out["variants"] = variants(args, n, st, ref, stream)
     if not args.no_e2e:
         out["e2e"] = end_to_end(args, s, n, world)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    if ref is not None:
+        out["variants"] = variants(args, n, ref, stream, dev)
+        del ref
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(out))
-    s.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -357,12 +428,17 @@ def roofline_and_profile(args, s, n):
                 "frac": achieved / hbm_peak if achieved else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
     roof.update({"kernel": top, "traffic": None, "launch_ms": per_launch_s * 1e3,
-                 "share": kms / tot})
+                 "share": kms / tot, "hbm_gbs_algorithmic": (bpu * units / per_launch_s / 1e9
+                                                             if bpu else None)})
     tr = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
     if os.path.exists(tr):
-        tt = _json.load(open(tr)).get(args.precision, {}).get(top)
+        tab = _json.load(open(tr))
+        key = args.workload if args.workload in tab else None
+        tt = tab.get(key, {}).get(args.precision, {}).get(top) if key else None
         if tt:
-            roof["traffic"] = tt * (units / 256 ** 3)
+            # measured DRAM bytes per unit (ncu on a smaller grid of the same workload,
+            # every array far larger than L2) times the units of one launch
+            roof["traffic"] = tt * units
 
     fp64_peak = s.probe_fma_peak("fp64")
     fp32_peak = s.probe_fma_peak("fp32")
@@ -404,47 +480,123 @@ def harvest_and_train(n_h, steps, stride, make_state, L, seed, epochs=4, cap=Non
                "loss_first": float(hist[0]), "loss_last": float(hist[-1])}
 
 
-def run_variant(n, L, st, precision, guess, steps, warmup, stream, weights=None):
+def train_guess(args):
+    """The network of the learned guess for the selected workload: about 1e7 states
+    harvested (every 4th cell after every inversion) from a --train-n^3 run of another
+    seed of the same workload, trained on the GPU."""
+    if args.workload == "turbulence":
+        mk = lambda m: turbulence_state(m, args.lorentz_max, seed=SEED + 1)
+        return harvest_and_train(args.train_n, args.train_steps, 4, mk, TURB_L, SEED + 2,
+                                 cap=10_000_000)
+    mk = lambda m: workload_state(m, args.wave)[1]
+    return harvest_and_train(64, 8, 4, mk, (1.0, 1.0, 1.0), SEED + 2)
+
+
+def l1_rel_device(sol, ref):
+    """L1 distance per primitive between a solver's state and a reference [8][...]
+    (device tensor) by echo_l1_error, normalised by the field scale as l1_rel does."""
+    import torch
+    l1 = sol.l1_error(ref)
+    out = []
+    for grp in ([0], [1, 2, 3], [4], [5, 6, 7]):
+        scale = float(torch.max(torch.abs(ref[grp])))
+        out += [float(l1[v]) / scale for v in grp]
+    return out
+
+
+def run_variant(args, n, precision, guess, stream, dev, ref=None, weights=None):
+    """One precision/guess variant of the headline run: same workload, warm-up and
+    timed steps; rate, Newton statistics and (with ref) the L1 distance to it."""
     import torch
     from paper_2401_03008_gb300 import echo
-    v = echo.Solver(n, n, n, L=L, precision=precision, guess=guess, stream=stream.cuda_stream)
+    L, st = state_for(args, n, device=dev)
+    v = echo.Solver(n, n, n, L=L, precision=precision, guess=guess, stream=stream.cuda_stream,
+                    uct=args.uct, ho=args.ho, rec=args.rec, rk_order=args.rk)
     if weights is not None:
         v.mlp_load(weights)
     v.set_state(*st)
-    v.step(warmup)
+    del st
+    torch.cuda.empty_cache()
+    v.step(args.warmup)
     v.diagnostics(reset=True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    v.step(steps)
+    v.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     d = v.diagnostics()
-    p = v.primitives()
+    r = {"value": n ** 3 * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+         "newton_it_fp64": d["newton_it_mean"], "newton_it_fp32": d["newton_it32_mean"],
+         "c2p_fallback_rate": d["c2p_fallbacks"] / max(d["c2p_calls"], 1),
+         "c2p_failures": d["c2p_failures"]}
+    if ref is not None:
+        r["l1_vs_fp64"] = l1_rel_device(v, ref)
     v.close()
-    return {"value": n ** 3 * steps / (ms * 1e-3), "ms_per_step": ms / steps,
-            "newton_it_fp64": d["newton_it_mean"], "newton_it_fp32": d["newton_it32_mean"],
-            "c2p_fallback_rate": d["c2p_fallbacks"] / max(d["c2p_calls"], 1),
-            "c2p_failures": d["c2p_failures"]}, p
+    del v
+    torch.cuda.empty_cache()
+    return r
 
 
-def variants(args, n, st, ref, stream):
-    """The mixed path and the mixed path with the learned guess on the same workload
-    and step count as the headline, with their L1 distance to the FP64 result."""
-    L = (1.0, 1.0, 1.0)
-    out = {}
-    r, p = run_variant(n, L, st, "mixed", "prev", args.steps, args.warmup, stream)
-    r["l1_vs_fp64"] = l1_rel(p, ref)
-    out["mixed"] = r
-    mk = lambda m: workload_state(m, args.wave)[1]
-    w, info = harvest_and_train(64, 8, 4, mk, L, 2401030081)
-    r, p = run_variant(n, L, st, "mixed", "mlp", args.steps, args.warmup, stream, w)
-    r["l1_vs_fp64"] = l1_rel(p, ref)
+def variants(args, n, ref, stream, dev):
+    """The mixed path, and the mixed path with the learned guess, on the same workload
+    and step count as the headline, with their L1 distance (per primitive, over the
+    field scale) to the FP64 state."""
+    out = {"mixed": run_variant(args, n, "mixed", "prev", stream, dev, ref)}
+    w, info = train_guess(args)
+    r = run_variant(args, n, "mixed", "mlp", stream, dev, ref, w)
     r["training"] = info
     out["mixed_mlp"] = r
+    out["l1_tolerance"] = ("L1(mixed - FP64) <= 1e-6 of each field's scale (the mixed path's "
+                           "stated bound)")
     return out
+
+
+def run_config_variant(args, n, precision, guess, steps, stream, dev, ref=None, weights=None,
+                       keep=False):
+    """A turbulence run of the benchmark plan: one warm-up step, then `steps` timed
+    steps; rate, Newton statistics, L1 distance to ref (when given); the primitives
+    on the device when keep."""
+    import torch
+    from paper_2401_03008_gb300 import echo
+    L, st = state_for(args, n, device=dev)
+    v = echo.Solver(n, n, n, L=L, precision=precision, guess=guess, stream=stream.cuda_stream)
+    if weights is not None:
+        v.mlp_load(weights)
+    v.set_state(*st)
+    del st
+    torch.cuda.empty_cache()
+    v.step(1)
+    v.diagnostics(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    try:
+        done, t = v.step(steps)
+        failed = None
+    except echo.EchoError as e:
+        done, t, failed = None, None, str(e)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    d = v.diagnostics()
+    r = {"ms_per_step": ms / steps, "cell_updates_per_s": n ** 3 * steps / (ms * 1e-3),
+         "t": d["t"], "newton_it_fp64": d["newton_it_mean"],
+         "newton_it_fp32": d["newton_it32_mean"],
+         "c2p_fallback_rate": d["c2p_fallbacks"] / max(d["c2p_calls"], 1),
+         "c2p_failures": d["c2p_failures"], "divb_max": d["divb_max"]}
+    if failed:
+        r["failed"] = failed
+    if ref is not None:
+        r["l1_vs_fp64"] = l1_rel_device(v, ref)
+    p = v.primitives(device=True) if keep else None
+    v.close()
+    del v
+    torch.cuda.empty_cache()
+    return r, p
 
 
 def run_config(args):
@@ -532,36 +684,25 @@ def run_config(args):
                     "period": c.period, "results": res})
     else:
         n = 512 if args.config == 4 else args.config5_n
-        L = (2 * np.pi,) * 3
-        seed = 2401_03008
-        tb = wl.Turbulence(n, seed=seed, lorentz_max=2.0)
-        st = (tb.prim5(), tb.bface_background(), tb.apot())
-        mk = lambda m: (lambda t: (t.prim5(), t.bface_background(), t.apot()))(
-            wl.Turbulence(m, seed=seed + 1, lorentz_max=2.0))
-        # 1e7 training states from 128^3 runs of another seed
-        w, info = harvest_and_train(128, 20, 4, mk, L, seed + 2, epochs=4, cap=10_000_000)
+        dev = "cuda:%d" % torch.cuda.current_device()
+        args.workload = "turbulence"
+        w, info = train_guess(args)
         res = {"training": info}
         runs = ([("fp64", "prev"), ("fp64", "cold"), ("fp64", "mlp"), ("mixed", "prev"),
                  ("mixed", "cold"), ("mixed", "mlp")] if args.config == 4 else
-                [("fp64", "prev"), ("mixed", "mlp"), ("mixed", "prev")])
-        prims = {}
+                [("fp64", "prev"), ("mixed", "prev"), ("mixed", "mlp")])
+        ref, ref_steps = None, None
         for prec, guess in runs:
             steps = args.config_steps if prec == "mixed" or args.config == 4 else args.config5_fp64_steps
-            r, p = run_variant(n, L, st, prec, guess, steps, 1, stream,
-                               w if guess == "mlp" else None)
+            keep = prec == "fp64" and guess == "prev"
+            r, p = run_config_variant(args, n, prec, guess, steps, stream, dev,
+                                      ref if steps == ref_steps else None,
+                                      w if guess == "mlp" else None, keep)
+            if keep:
+                ref, ref_steps = p, steps
             r["steps"] = steps
             res["%s_%s" % (prec, guess)] = r
-            prims[(prec, guess)] = p
-        if args.config == 5:
-            # the mixed runs and the FP64 run may differ in step count: compare the
-            # mixed variants with each other and report the FP64 rate
-            res["mixed_mlp"]["l1_vs_mixed_prev"] = l1_rel(prims[("mixed", "mlp")], prims[("mixed", "prev")])
-        else:
-            res["mixed_prev"]["l1_vs_fp64_prev"] = l1_rel(prims[("mixed", "prev")], prims[("fp64", "prev")])
-            res["mixed_mlp"]["l1_vs_fp64_prev"] = l1_rel(prims[("mixed", "mlp")], prims[("fp64", "prev")])
-        out.update({"workload": "decaying Alfvenic turbulence, %d^3, sigma0 = 10, beta0 = 1, "
-                                "mean |dB|/B0 = 0.5, max Lorentz factor 2, |k| <= 4, seed %d"
-                                % (n, seed), "results": res})
+        out.update({"workload": workload_name(args, n), "results": res})
     print(json.dumps(out))
 
 
@@ -671,12 +812,13 @@ def run_blocks(args, timed, sp):
 
 def end_to_end(args, s, n, world):
     """The same metric through the C ABI with host buffers: every step uploads the
-    state from pinned host memory, advances one step and reads the state back."""
+    state from pinned host memory (echo_set_conserved), advances one step and reads
+    the state back (echo_get_state)."""
     import torch
     pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
     cons, bf, w = pin((5, n, n, n)), pin((3, n, n, n)), pin((n, n, n))
     _, _, _, t0s, st0 = s.get_state(cons, bf, w)
-    ke = max(2, min(args.steps, 5))
+    ke = 2
     torch.cuda.synchronize()
     q0 = time.perf_counter()
     for _ in range(ke):
@@ -686,6 +828,7 @@ def end_to_end(args, s, n, world):
     el = time.perf_counter() - q0
     _, value = job_rate(el * 1e3, n ** 3 * ke, world)  # the slowest rank's time
     by = cons.nbytes + bf.nbytes + w.nbytes
+    del cons, bf, w
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": by,
             "d2h_bytes_per_step": by, "steps": ke}
 

@@ -153,9 +153,10 @@ echo_status echo_get_primitives(echo_ctx *ctx, double *out, int ptr_kind);
 echo_status echo_get_state(echo_ctx *ctx, double *cons5, double *bface, double *w,
                            double *t, long *step, int ptr_kind);
 
-/* Resume from a checkpoint written by echo_get_state (same layouts).  w may be NULL
- * (the guess is then rebuilt by a cold inversion).  A resumed run is bit-identical
- * to an uninterrupted one. */
+/* Resume from a checkpoint written by echo_get_state (same layouts).  w may be NULL:
+ * the first inversion then starts from the learned guess if one is loaded
+ * (echo_mlp_load), else from W0 = U.  A resumed run with w is bit-identical to an
+ * uninterrupted one. */
 echo_status echo_set_conserved(echo_ctx *ctx, const double *cons5, const double *bface,
                                const double *w, double t, long step, int ptr_kind);
 
@@ -215,10 +216,19 @@ typedef struct {
     unsigned long seed;  /* offset of the per-epoch batch permutation */
 } echo_train_cfg;
 
-/* Load parameters (host, n = ECHO_MLP_NPARAM floats) into the context; used when
- * c2p_guess = ECHO_GUESS_MLP.  Cells whose guess is unusable fall back to the
+/* Load parameters (host, n = ECHO_MLP_NPARAM floats) into the context.  The
+ * inversion then starts Newton from the learned guess, computed inside the
+ * inversion kernel, at every cell when c2p_guess = ECHO_GUESS_MLP, and in any case
+ * for the first inversion after echo_set_conserved without a stored W (where no
+ * previous solution exists).  Cells whose guess is unusable fall back to the
  * previous W and are counted (echo_diag.c2p_fallbacks). */
 echo_status echo_mlp_load(echo_ctx *ctx, const float *weights, long n);
+
+/* The learned guess W0 = U y of every cell for the current state, out [nz][ny][nx]
+ * (host or device, ptr_kind): the value the inversion starts from when it uses the
+ * network (the same device code, rounded through float).  ECHO_ERR_STATE before
+ * echo_mlp_load or echo_set_state; allocates n floats on the first call. */
+echo_status echo_mlp_guess(echo_ctx *ctx, double *out, int ptr_kind);
 
 /* Inference on its own: y[n] (device) for features feats[n][5] (device) with the
  * parameters weights (host), on stream (NULL: default stream). */
@@ -240,9 +250,11 @@ echo_status echo_mlp_train(const float *feats, const float *target, long n,
                            void *stream);
 
 /* Advance nsteps SSP-RK3 steps (as echo_step) and, after every inversion, append the
- * features and the converged W/U of every stride-th cell (offset rotating between
- * calls) to feats[capacity][5] and target[capacity] (device).  *count receives the
- * number of states written (at most capacity). */
+ * features and the converged W/U of every stride-th cell (cells offset + q stride,
+ * the offset rotating between inversions) to feats[capacity][5] and
+ * target[capacity] (device): in cell order within an inversion and in inversion
+ * order across them, so the buffers are deterministic.  *count receives the number
+ * of states written (at most capacity). */
 echo_status echo_mlp_harvest(echo_ctx *ctx, int nsteps, long stride, float *feats, float *target,
                              long capacity, long *count);
 
@@ -259,15 +271,18 @@ echo_status echo_mlp_harvest(echo_ctx *ctx, int nsteps, long stride, float *feat
  *   nx, ny, nz, lx, ly, lz, ho: the grid, as in echo_config.
  *   stream: cudaStream_t to run on (NULL: the default stream); the call returns
  *         after the stream has finished the reduction.
- *   out: 11 doubles, host (out_kind = ECHO_PTR_HOST) or device memory.
+ *   out: 11 doubles, host (out_kind = ECHO_PTR_HOST) or device memory of the
+ *         current device (ECHO_PTR_DEVICE).
  * No memory is allocated: the block partial sums live in a fixed array of about
- * 0.8 MB inside the library, which every GPU that loads the library holds until
+ * 0.36 MB inside the library, which every GPU that loads the library holds until
  * the process exits.  It limits the grid to 1,048,576 cells; larger grids return
  * ECHO_ERR_ARG.  Every call shares that array, so calls that overlap on the GPU
  * (several streams or host threads at once) race and must be serialised by the
- * caller.  The first call on a device looks up the array's device address; make
- * it before any stream capture.  Errors: ECHO_ERR_ARG (sizes, NULL or non-device
- * inputs), ECHO_ERR_CUDA; the text is in echo_last_error(NULL).  The sums agree
+ * caller.  The first call on a device looks up the array's device address and
+ * keeps it for the process (it belongs to the device's primary context, which must
+ * not be reset in between); make that first call before any stream capture.
+ * Errors: ECHO_ERR_ARG (sizes, NULL, non-device inputs, or a non-device out with
+ * ECHO_PTR_DEVICE), ECHO_ERR_CUDA; the text is in echo_last_error(NULL).  The sums agree
  * with echo_diagnostics to rounding (the summation order differs). */
 echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, int nx,
                                      int ny, int nz, double lx, double ly, double lz, int ho,

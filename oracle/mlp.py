@@ -81,3 +81,16 @@ def loss_grad(theta, x, t, bf=False):
     g["b1"] = dz1.sum(axis=0)
     g["W1"] = dz1.T @ x
     return loss, pack(g)
+
+
+def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, 2015), step number t >= 1:
+    m <- beta1 m + (1 - beta1) g,  v <- beta2 v + (1 - beta2) g^2,
+    theta <- theta - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+    Returns the new (theta, m, v); the inputs are not modified."""
+    g = np.asarray(grad, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return np.asarray(theta, dtype=np.float64) - lr * mhat / (np.sqrt(vhat) + eps), m, v

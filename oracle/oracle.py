@@ -211,12 +211,21 @@ class Grid:
         self.t = 0.0
         self.steps = 0
 
+    def _guess_ptr(self):
+        """the caller's guess array (required when guess == GUESS_ARRAY)"""
+        if self.cfg.guess == GUESS_ARRAY:
+            if self.guessarr is None or self.guessarr.size != self.n:
+                raise ValueError("guess = GUESS_ARRAY needs guessarr of %d values" % self.n)
+            self.guessarr = np.ascontiguousarray(self.guessarr, dtype=np.float64)
+            return _p(self.guessarr)
+        return None
+
     def rhs(self, with_prims=False):
         rc = np.zeros((5,) + self.shape)
         rb = np.zeros((3,) + self.shape)
         prim = np.zeros((8,) + self.shape)
         amax = C.c_double()
-        ga = _p(self.guessarr) if self.guessarr is not None else None
+        ga = self._guess_ptr()
         bad = lib().orc_rhs(C.byref(self.cfg), _p(self.cons), _p(self.bf), _p(self.W), ga,
                             _p(rc), _p(rb), _p(prim), C.byref(amax), C.byref(self.stats))
         if with_prims:
@@ -227,7 +236,7 @@ class Grid:
         bad = 0
         dt = C.c_double()
         t = C.c_double(self.t)
-        ga = _p(self.guessarr) if self.guessarr is not None else None
+        ga = self._guess_ptr()
         self.dts = []
         for _ in range(nsteps):
             if t.value >= t_end:

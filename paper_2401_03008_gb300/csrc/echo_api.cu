@@ -323,6 +323,7 @@ echo_status echo_set_state(echo_ctx *c, const double *prim, const double *bface,
     if ((st = sync_check(c))) return st;
     if (res[9] != 0.0) return fail(c, ECHO_ERR_NONFINITE, "initial state has non-finite values");
     c->has_state = true;
+    c->w_cold = false;
     return ECHO_OK;
 }
 
@@ -332,7 +333,7 @@ echo_status echo_set_state(echo_ctx *c, const double *prim, const double *bface,
 struct Harvest {
     long stride, capacity;
     float *feats, *target;
-    unsigned long long *count;
+    long count;  // states offered so far (slots base + q are filled while below capacity)
     long calls;
 };
 
@@ -343,11 +344,15 @@ void launch_stage(echo_ctx *c, int stage, Harvest *hv)
 {
     static const char *names[4] = {"stage", "stage 1", "stage 2", "stage 3"};
     echo::Range r(names[stage < 4 ? stage : 0]);
-    Path<R>::int_c2p(c, stage, 1);
+    // the learned guess: everywhere when selected, else for the first inversion after
+    // a resume without a stored W (when the weights are loaded)
+    const bool learned = c->cfg.c2p_guess == ECHO_GUESS_MLP || (stage == 1 && c->w_cold);
+    Path<R>::int_c2p(c, stage, 1, learned);
+    if (stage == 1) c->w_cold = false;
     if (hv) {
         long off = (hv->calls * 7919L) % hv->stride;
-        echo::launch_mlp_harvest(c, hv->stride, off, hv->feats, hv->target, hv->capacity,
-                                 hv->count);
+        hv->count += echo::launch_mlp_harvest(c, hv->stride, off, hv->feats, hv->target,
+                                              hv->count, hv->capacity);
         hv->calls++;
     }
     Path<R>::sweeps(c, stage == 1);
@@ -403,23 +408,28 @@ echo_status run_steps(echo_ctx *c, int max_steps, double t_end, int *steps_done,
     // steps are replays of one captured step: a full step's launches as one graph
     // launch.  Every kernel reads the step state (dt, halt flag, counters) from the
     // device scalars, so the replays behave exactly like the launches.
+    // A step whose first inversion starts from the learned guess because W holds no
+    // previous solution is launched directly; the replays follow.
     const bool graph = !finite_end && !hv && !c->prof_on && max_steps >= 2;
-    if (graph && !c->step_graph && !c->graph_failed) build_step_graph(c);
-    if (graph && c->step_graph) {
-        for (int s = 0; s < max_steps; s++) {
-            CK(cudaGraphLaunch(c->step_graph, c->stream));
-            c->launches += c->graph_kernels;
+    for (int s = 0; s < max_steps;) {
+        if (graph && !c->w_cold) {
+            if (!c->step_graph && !c->graph_failed) build_step_graph(c);
+            if (c->step_graph) {
+                for (; s < max_steps; s++) {
+                    CK(cudaGraphLaunch(c->step_graph, c->stream));
+                    c->launches += c->graph_kernels;
+                }
+                break;
+            }
         }
-    } else {
-        for (int s = 0; s < max_steps; s++) {
-            for (int stage = 1; stage <= c->cfg.rk_order; stage++) {
-                if (c->mixed) launch_stage<float>(c, stage, hv);
-                else launch_stage<double>(c, stage, hv);
-            }
-            if (finite_end) {
-                if ((st = read_sc(c, &h))) return st;
-                if (h.halt) break;
-            }
+        for (int stage = 1; stage <= c->cfg.rk_order; stage++) {
+            if (c->mixed) launch_stage<float>(c, stage, hv);
+            else launch_stage<double>(c, stage, hv);
+        }
+        s++;
+        if (finite_end) {
+            if ((st = read_sc(c, &h))) return st;
+            if (h.halt) break;
         }
     }
     if ((st = sync_check(c))) return st;
@@ -462,18 +472,9 @@ echo_status echo_mlp_harvest(echo_ctx *c, int nsteps, long stride, float *feats,
         return fail(c, ECHO_ERR_ARG, "echo_mlp_harvest: bad buffers, stride or capacity");
     echo_status st = select_device(c);
     if (st) return st;
-    Harvest hv{stride, capacity, feats, target, nullptr, 0};
-    if (cudaMalloc((void **)&hv.count, sizeof(unsigned long long)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, ECHO_ERR_OOM, "echo_mlp_harvest: counter");
-    }
-    cudaMemsetAsync(hv.count, 0, sizeof(unsigned long long), c->stream);
+    Harvest hv{stride, capacity, feats, target, 0, 0};
     st = run_steps(c, nsteps, INFINITY, nullptr, nullptr, &hv);
-    unsigned long long cnt = 0;
-    cudaMemcpyAsync(&cnt, hv.count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream);
-    cudaStreamSynchronize(c->stream);
-    cudaFree(hv.count);
-    if (count) *count = (long)(cnt < (unsigned long long)capacity ? cnt : capacity);
+    if (count) *count = hv.count < capacity ? hv.count : capacity;
     return st;
 }
 
@@ -509,8 +510,10 @@ echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *am
             df = c->stage8 + 5 * n;
         }
     }
+    const bool learned = c->cfg.c2p_guess == ECHO_GUESS_MLP || c->w_cold;
+    c->w_cold = false;
     if (c->mixed) {
-        Path<float>::int_c2p(c, 0, 1);
+        Path<float>::int_c2p(c, 0, 1, learned);
         Path<float>::sweeps(c, 1);
         Path<float>::uct(c);
         if (c->g.uct) {
@@ -520,7 +523,7 @@ echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *am
             Path<float>::rhs_out(c, tmp8);
         }
     } else {
-        Path<double>::int_c2p(c, 0, 1);
+        Path<double>::int_c2p(c, 0, 1, learned);
         Path<double>::sweeps(c, 1);
         Path<double>::uct(c);
         if (c->g.uct) {
@@ -567,6 +570,33 @@ echo_status echo_get_primitives(echo_ctx *c, double *out, int ptr_kind)
     return sync_check(c);
 }
 
+echo_status echo_mlp_guess(echo_ctx *c, double *out, int ptr_kind)
+{
+    if (!c || !out) return fail(c, ECHO_ERR_ARG, "ctx or out is NULL");
+    if (!c->has_state) return fail(c, ECHO_ERR_STATE, "no state");
+    if (!c->mlp_w) return fail(c, ECHO_ERR_STATE, "echo_mlp_guess before echo_mlp_load");
+    echo_status st = select_device(c);
+    if (st) return st;
+    const long n = c->g.n;
+    if (!c->guess) {
+        if (cudaMalloc((void **)&c->guess, n * sizeof(float)) != cudaSuccess) {
+            c->guess = nullptr;
+            cudaGetLastError();
+            return fail(c, ECHO_ERR_OOM, "echo_mlp_guess: %ld floats do not fit", n);
+        }
+    }
+    double *d = out;
+    if (ptr_kind != ECHO_PTR_DEVICE) {
+        if ((st = ensure_stage(c))) return st;
+        d = c->stage8;
+    }
+    if (c->mixed) Path<float>::mlp_guess(c);
+    else Path<double>::mlp_guess(c);
+    echo::launch_widen(c, d, c->guess, n);
+    if ((st = output(c, out, d, n, ptr_kind))) return st;
+    return sync_check(c);
+}
+
 echo_status echo_get_state(echo_ctx *c, double *cons5, double *bface, double *w, double *t,
                            long *step, int ptr_kind)
 {
@@ -597,6 +627,7 @@ echo_status echo_set_conserved(echo_ctx *c, const double *cons5, const double *b
     CK(cudaMemcpyAsync(c->Bf, bface, 3 * n * sizeof(double), k, c->stream));
     if (w) CK(cudaMemcpyAsync(c->W, w, n * sizeof(double), k, c->stream));
     else echo::launch_w_from_cold(c);
+    c->w_cold = w == nullptr;
     echo::launch_bf32(c);
     DevScalars h;
     if ((st = read_sc(c, &h))) return st;

@@ -45,7 +45,10 @@ struct echo_ctx {
     double *dres;           // reduction results (device)
     double *stage8;         // staging for host outputs [8][n] (allocated on demand)
     void *mlp_w;            // learned-guess weights in their device form, or NULL
-    float *guess;           // learned guesses [n] (allocated with the weights)
+    float *guess;           // learned guesses [n] for echo_mlp_guess (allocated on demand)
+    // W holds no previous solution (a checkpoint resumed without it: W = U); the
+    // next inversion starts from the learned guess if the weights are loaded
+    bool w_cold;
 
     bool has_state;
     long launches;
@@ -105,10 +108,12 @@ constexpr int DIAG_Q = 24;  // quantities per block partial
 // Per-precision kernel launchers (one translation unit per precision).
 template <typename R>
 struct Path {
-    // (learned guesses when selected and loaded, then) INT + C2P into the work prims
-    // (R).  stage: 1..3 (0 for a one-off call); update_w: store the converged W as
-    // the next warm guess.
-    static void int_c2p(echo_ctx *c, int stage, int update_w);
+    // INT + C2P into the work prims (R).  stage: 1..3 (0 for a one-off call);
+    // update_w: store the converged W as the next warm guess; learned: start Newton
+    // from the learned guess (computed in the kernel) when the weights are loaded.
+    static void int_c2p(echo_ctx *c, int stage, int update_w, bool learned);
+    // the learned guesses of the current state into c->guess (echo_mlp_guess)
+    static void mlp_guess(echo_ctx *c);
     // sweeps + DER (steps 2-3), want_amax on the first stage of a step
     static void sweeps(echo_ctx *c, int want_amax);
     // UCT edge fields (step 4, first half)
@@ -133,6 +138,8 @@ void launch_diag_mode(echo_ctx *c, int mode, const double *a, const double *b);
 void launch_copy_state(echo_ctx *c, double *dst_u, double *dst_b, const double *src_u,
                        const double *src_b);
 void launch_w_from_cold(echo_ctx *c);
+// out[q] = in[q] widened to double, q < m
+void launch_widen(echo_ctx *c, double *out, const float *in, long m);
 // refresh the float copy of the face field (mixed path) after the state changed
 void launch_bf32(echo_ctx *c);
 double probe_fma_peak(echo_ctx *c, int fp64);
@@ -140,8 +147,9 @@ double probe_fma_peak(echo_ctx *c, int fp64);
 void set_global_error(const char *msg);
 // drop the captured step graph (the launch set changed)
 void drop_step_graph(echo_ctx *c);
-// harvest of training states (features, converged W/U)
-void launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,
-                        long capacity, unsigned long long *count);
+// harvest of training states (features, converged W/U) of cells offset + q stride
+// into slots base + q (those below capacity); returns the number of such cells
+long launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,
+                        long base, long capacity);
 
 }  // namespace echo

@@ -68,8 +68,9 @@ void launch_curl_apot(echo_ctx *c, const double *apot)
 void launch_prims_out(echo_ctx *c, double *out8)
 {
     C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, ECHO_GUESS_PREV, 0};
-    launch(c, K_C2P, k_int_c2p<double>, nblocks(c->g.n, BS), BS, 0, c->g, (const double *)c->U,
-           (const double *)c->Bf, c->W, (const float *)nullptr, out8, par, c->sc, 0, 0, 0);
+    launch(c, K_C2P, k_int_c2p<double, false>, nblocks(c->g.n, BS), BS, 0, c->g,
+           (const double *)c->U, (const double *)c->Bf, c->W, (const MlpDev *)nullptr, out8, par,
+           c->sc, 0, 0, 0);
 }
 
 __global__ void __launch_bounds__(BS)
@@ -99,6 +100,17 @@ void launch_bf32(echo_ctx *c)
     if (!c->Bf32) return;
     long m = 3 * c->g.n;
     launch(c, K_MISC, k_to_float, nblocks(m, BS), BS, 0, m, (const double *)c->Bf, c->Bf32);
+}
+
+__global__ void __launch_bounds__(BS) k_widen(long m, const float *__restrict__ in, double *__restrict__ out)
+{
+    long q = blockIdx.x * (long)BS + threadIdx.x;
+    if (q < m) out[q] = to_f64(in[q]);
+}
+
+void launch_widen(echo_ctx *c, double *out, const float *in, long m)
+{
+    launch(c, K_MISC, k_widen, nblocks(m, BS), BS, 0, m, in, out);
 }
 
 // cold guess W0 = U for a resumed state without a stored guess

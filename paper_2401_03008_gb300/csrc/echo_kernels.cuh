@@ -92,13 +92,15 @@ __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
 // ---------------------------------------------------------------------------
 // step 1: INT + C2P
 // ---------------------------------------------------------------------------
-// guess: the learned starting guesses W0 (one float per cell, from k_mlp_guess) when
-// that guess is selected, else NULL.  An unusable guess falls back to the previous
-// W and is counted.
-template <typename R>
-__global__ void __launch_bounds__(BS, minb_c2p(sizeof(R)))
+// MLP: the learned starting guess is computed in the kernel from the cell's
+// conserved state and field (the network's parameters mw in global memory, read
+// through L1); a guess that is unusable falls back to the previous W and is counted.
+// The network runs on whole warps, before the divergent Newton iteration: lanes
+// past the grid evaluate it on a placeholder state.
+template <typename R, bool MLP>
+__global__ void __launch_bounds__(BS, MLP ? 2 : minb_c2p(sizeof(R)))
 k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
-          double *__restrict__ W, const float *__restrict__ guess, R *__restrict__ prim,
+          double *__restrict__ W, const MlpDev *__restrict__ mw, R *__restrict__ prim,
           C2PParams par, DevScalars *sc, int stage, int update_w, int count)
 {
     // the flag is set by other blocks of this launch: read it once per warp so that
@@ -108,19 +110,22 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
     long c = blockIdx.x * (long)BS + threadIdx.x;
     unsigned it = 0, it32 = 0;
     bool active = c < n, bad = false, fb = false, own = false;
+    double u[5] = {1.0, 0.0, 0.0, 0.0, 2.0}, B[3] = {0.0, 0.0, 0.0};
     if (active) {
         int i, j, k;
         coords(g, c, i, j, k);
         own = owned(g, i, j, k);
-        double B[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) B[d] = cell_field(g, Bf, c, i, j, k, d);
-        double u[5];
 #pragma unroll
         for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
+    }
+    double Wml = 0.0;
+    if (MLP) Wml = mlp_guess_warp(*mw, u, B, threadIdx.x & 31);
+    if (active) {
         double W0;
-        if (guess) {
-            W0 = to_f64(guess[c]);
+        if (MLP) {
+            W0 = Wml;
             C2PInv q;
             q.D = u[0];
             q.S2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
@@ -173,10 +178,11 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
     }
 }
 
-// Learned Newton starting guesses W0 = U y for every cell.  Persistent blocks: the
-// weights go to shared memory once per block, which then walks the grid in steps
-// of the whole launch.  BT: precision of the face field read for the features
-// (the float mirror on the mixed path).
+// Learned Newton starting guesses W0 = U y of every cell into guess[n] (the values
+// the inversion kernel computes in place; used by echo_mlp_guess).  Persistent
+// blocks: the weights go to shared memory once per block, which then walks the grid
+// in steps of the whole launch.  BT: precision of the face field read for the
+// features (the float mirror on the mixed path, as in the step).
 constexpr int MLP_BS = 128;
 
 template <typename BT>
@@ -197,10 +203,8 @@ k_mlp_guess(Grid g, const double *__restrict__ U, const BT *__restrict__ Bf,
             for (int d = 0; d < 3; d++) B[d] = cell_field(g, Bf, c, i, j, k, d);
             for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
         }
-        float x[NIN];
-        mlp_features(u, B, x);
-        const float y = mlp_warp_forward(sw, x, lane);
-        if (c < n) guess[c] = to_f32(u[4] * to_f64(y));
+        const double w0 = mlp_guess_warp(sw, u, B, lane);
+        if (c < n) guess[c] = to_f32(w0);
     }
 }
 
@@ -533,23 +537,31 @@ template <> inline const double *face_field<double>(echo_ctx *c) { return c->Bf;
 template <> inline const float *face_field<float>(echo_ctx *c) { return c->Bf32; }
 
 template <typename R>
-void Path<R>::int_c2p(echo_ctx *c, int stage, int update_w)
+void Path<R>::int_c2p(echo_ctx *c, int stage, int update_w, bool learned)
 {
     // the mixed path refines the guess with FP32 Newton iterations first
     C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, c->cfg.c2p_guess, c->mixed ? 1 : 0};
-    const bool mlp = par.guess == ECHO_GUESS_MLP && c->mlp_w && c->guess;
-    if (par.guess == ECHO_GUESS_MLP && !mlp) par.guess = ECHO_GUESS_PREV;
-    if (mlp) {
-        // persistent grid: as many blocks as can be resident at once (sized when the
-        // weights were loaded, outside any stream capture)
-        unsigned nb = nblocks(c->g.n, MLP_BS);
-        if (c->mlp_blocks && nb > c->mlp_blocks) nb = c->mlp_blocks;
-        launch(c, K_MLP, k_mlp_guess<R>, nb, MLP_BS, 0, c->g, (const double *)c->U,
-               face_field<R>(c), (const MlpDev *)c->mlp_w, c->guess);
-    }
-    launch(c, K_C2P, k_int_c2p<R>, nblocks(c->g.n, BS), BS, 0, c->g, (const double *)c->U,
-           (const double *)c->Bf, c->W, mlp ? (const float *)c->guess : (const float *)nullptr,
-           (R *)c->prim, par, c->sc, stage, update_w, 1);
+    const bool mlp = learned && c->mlp_w;
+    if (par.guess == ECHO_GUESS_MLP) par.guess = ECHO_GUESS_PREV;
+    if (mlp)
+        launch(c, K_C2P, k_int_c2p<R, true>, nblocks(c->g.n, BS), BS, 0, c->g,
+               (const double *)c->U, (const double *)c->Bf, c->W, (const MlpDev *)c->mlp_w,
+               (R *)c->prim, par, c->sc, stage, update_w, 1);
+    else
+        launch(c, K_C2P, k_int_c2p<R, false>, nblocks(c->g.n, BS), BS, 0, c->g,
+               (const double *)c->U, (const double *)c->Bf, c->W, (const MlpDev *)nullptr,
+               (R *)c->prim, par, c->sc, stage, update_w, 1);
+}
+
+template <typename R>
+void Path<R>::mlp_guess(echo_ctx *c)
+{
+    // persistent grid: as many blocks as can be resident at once (sized when the
+    // weights were loaded)
+    unsigned nb = nblocks(c->g.n, MLP_BS);
+    if (c->mlp_blocks && nb > c->mlp_blocks) nb = c->mlp_blocks;
+    launch(c, K_MLP, k_mlp_guess<R>, nb, MLP_BS, 0, c->g, (const double *)c->U, face_field<R>(c),
+           (const MlpDev *)c->mlp_w, c->guess);
 }
 
 template <typename R>

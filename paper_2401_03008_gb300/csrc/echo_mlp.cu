@@ -64,17 +64,20 @@ __global__ void k_mlp_build(const float *__restrict__ p, MlpDev *w)
     }
 }
 
-// features and the converged W/U of a strided subset of cells, appended to a
-// caller buffer (harvest of training states from the solver's own inversions)
+// features and the converged W/U of a strided subset of cells, written to a caller
+// buffer (harvest of training states from the solver's own inversions).  Cell
+// q stride + offset goes to slot base + q, so the buffer holds the states in cell
+// order within each inversion and in inversion order across calls.
 __global__ void __launch_bounds__(256)
 k_mlp_harvest(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
               const double *__restrict__ W, long stride, long offset, float *feats,
-              float *target, long capacity, unsigned long long *count)
+              float *target, long base, long capacity)
 {
     const long q = blockIdx.x * 256L + threadIdx.x;
     const long c = q * stride + offset;
     const long n = g.n;
-    if (c >= n) return;
+    const long slot = base + q;
+    if (c >= n || slot >= capacity) return;
     int i, j, k;
     coords(g, c, i, j, k);
     double B[3];
@@ -83,8 +86,6 @@ k_mlp_harvest(Grid g, const double *__restrict__ U, const double *__restrict__ B
     for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
     float x[NIN];
     mlp_features(u, B, x);
-    unsigned long long slot = atomicAdd(count, 1ull);
-    if (slot >= (unsigned long long)capacity) return;
     for (int f = 0; f < NIN; f++) feats[slot * NIN + f] = x[f];
     target[slot] = (float)(W[c] / u[4]);
 }
@@ -368,11 +369,6 @@ echo_status echo_mlp_load(echo_ctx *c, const float *weights, long n)
         cudaGetLastError();
         return ECHO_ERR_OOM;
     }
-    if (!c->guess && cudaMalloc((void **)&c->guess, c->g.n * sizeof(float)) != cudaSuccess) {
-        c->guess = nullptr;
-        cudaGetLastError();
-        return ECHO_ERR_OOM;
-    }
     float *dp = nullptr;
     if (cudaMalloc((void **)&dp, NPARAM * sizeof(float)) != cudaSuccess) return ECHO_ERR_OOM;
     cudaMemcpyAsync(dp, weights, NPARAM * sizeof(float), cudaMemcpyHostToDevice, c->stream);
@@ -380,8 +376,8 @@ echo_status echo_mlp_load(echo_ctx *c, const float *weights, long n)
     c->launches++;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     cudaFree(dp);
-    // the persistent grid of the guess kernel, and a step graph without that kernel
-    // no longer matches the launches
+    // the persistent grid of the guess kernel of echo_mlp_guess; a captured step
+    // graph holds the inversion kernel without the network and no longer matches
     c->mlp_blocks = c->mixed ? echo::Path<float>::mlp_grid(c) : echo::Path<double>::mlp_grid(c);
     echo::drop_step_graph(c);
     return e == cudaSuccess ? ECHO_OK : ECHO_ERR_CUDA;
@@ -478,14 +474,16 @@ echo_status echo_mlp_train(const float *feats, const float *target, long n,
 
 namespace echo {
 
-void launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,
-                        long capacity, unsigned long long *count)
+long launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,
+                        long base, long capacity)
 {
-    long m = (c->g.n - offset + stride - 1) / stride;
-    if (m <= 0) return;
-    launch(c, K_MISC, k_mlp_harvest, nblocks(m, 256), 256, 0, c->g, (const double *)c->U,
-           (const double *)c->Bf, (const double *)c->W, stride, offset, feats, target, capacity,
-           count);
+    const long m = (c->g.n - offset + stride - 1) / stride;
+    if (m <= 0) return 0;
+    if (base < capacity)
+        launch(c, K_MISC, k_mlp_harvest, nblocks(m, 256), 256, 0, c->g, (const double *)c->U,
+               (const double *)c->Bf, (const double *)c->W, stride, offset, feats, target, base,
+               capacity);
+    return m;
 }
 
 }  // namespace echo

@@ -174,6 +174,19 @@ __device__ __forceinline__ float mlp_warp_forward(const MlpDev &w, const float *
     return (q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3]) + w.b3;
 }
 
+// Learned starting guess of the lane's cell, W0 = U y, rounded through float (the
+// precision of the network's output).  Every lane of the warp calls it together
+// (the product is warp-wide); a lane without a cell passes any finite state and
+// ignores the result.  w: the parameters in shared or global memory.
+__device__ __forceinline__ double mlp_guess_warp(const MlpDev &w, const double *u,
+                                                 const double *B, int lane)
+{
+    float x[NIN];
+    mlp_features(u, B, x);
+    const float y = mlp_warp_forward(w, x, lane);
+    return to_f64(to_f32(u[4] * to_f64(y)));
+}
+
 // the inference prefix of the parameters into shared memory (sw: MLP_INFER_BYTES,
 // 16-byte aligned); the block synchronises before returning
 __device__ __forceinline__ const MlpDev &load_mlp_shared(unsigned char *sw, const MlpDev *w)

@@ -8,8 +8,9 @@
 // own device arrays and an output buffer; the block partial sums live in the
 // file-scope array below instead of in memory the library would allocate.
 //
-// The scratch array: NA_MAX_BLOCKS partials of NA_Q doubles plus one result row,
-// about 0.8 MB, held by every GPU that loads the library until the process exits.
+// The scratch array: NA_MAX_BLOCKS partials of NA_Q = 11 doubles plus one result
+// row, about 0.36 MB, held by every GPU that loads the library until the process
+// exits.
 // One block of 256 threads reduces 256 cells, so grids up to NA_MAX_CELLS
 // (1,048,576 cells, e.g. 101^3) fit; larger grids are rejected with ECHO_ERR_ARG.
 // Every call shares the array and overwrites every slot it later reads (nothing
@@ -19,7 +20,10 @@
 // Set-up: the first call on a device looks up the device address of the array
 // with cudaGetSymbolAddress (the host-side name of a __device__ array is not a
 // device address) and caches it for that device.  Make that first call before any
-// stream capture.
+// stream capture.  The cached address belongs to the device's primary context: a
+// caller that resets the device (cudaDeviceReset) and keeps using the library in
+// the same process would find it stale, so this entry point is for processes that
+// keep their primary context alive.
 #include <mutex>
 
 #include "echo_internal.h"
@@ -28,7 +32,7 @@ namespace {
 
 constexpr int NA_THREADS = 256;
 constexpr int NA_MAX_BLOCKS = 4096;
-constexpr int NA_Q = 24;
+constexpr int NA_Q = 11;  // per block: 10 sums, then max |div B|
 constexpr long NA_MAX_CELLS = (long)NA_MAX_BLOCKS * NA_THREADS;
 constexpr int NA_OUT = 11;  // tot[8], divb_max, divb_l2, nonfinite
 constexpr int NA_MAX_DEVICES = 64;
@@ -50,7 +54,8 @@ __device__ __forceinline__ void na_add(NaPair &p, double x)
     p.s = t;
 }
 
-// one partial per block of 256 cells: 10 compensated sums (as s and c) + max |div B|
+// one partial per block of 256 cells: 10 plain sums (a fixed tree over the block's
+// threads; the compensation happens across blocks, in k_na_final) + max |div B|
 __global__ void __launch_bounds__(NA_THREADS)
 k_na_partial(echo::Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
              double *scratch)
@@ -151,16 +156,17 @@ echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, i
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
         return na_fail(ECHO_ERR_CUDA, "echo_diagnostics_noalloc: no current CUDA device");
-    // the inputs must be device memory of the current device
-    const void *ins[2] = {cons5, bface};
+    // the inputs (and a device output) must be device memory of the current device
+    const void *ins[3] = {cons5, bface, out_kind == ECHO_PTR_DEVICE ? (const void *)out : nullptr};
     for (const void *p : ins) {
+        if (!p) continue;
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice ||
             a.device != dev) {
             cudaGetLastError();
             return na_fail(ECHO_ERR_ARG,
-                           "echo_diagnostics_noalloc: inputs must be device memory of the "
-                           "current device");
+                           "echo_diagnostics_noalloc: inputs (and a device out) must be device "
+                           "memory of the current device");
         }
     }
     double *scratch;

@@ -29,7 +29,8 @@ EXPORTS = ["echo_config_default", "echo_create", "echo_destroy", "echo_set_state
            "echo_set_conserved", "echo_diagnostics", "echo_l1_error", "echo_profile_enable",
            "echo_profile_read", "echo_launches", "echo_probe_fma_peak", "echo_stream",
            "echo_last_error", "echo_diagnostics_noalloc", "echo_mlp_load", "echo_mlp_forward",
-           "echo_mlp_grad", "echo_mlp_train", "echo_mlp_harvest", "echo_decomp_min_halo",
+           "echo_mlp_grad", "echo_mlp_train", "echo_mlp_harvest", "echo_mlp_guess",
+           "echo_decomp_min_halo",
            "echo_decomp_create", "echo_decomp_destroy", "echo_decomp_set_state",
            "echo_decomp_step", "echo_decomp_get_state", "echo_decomp_get_primitives",
            "echo_decomp_counters", "echo_decomp_last_error"]
@@ -115,6 +116,7 @@ def lib():
     L.echo_mlp_grad.argtypes = [fp, vp, vp, C.c_long, fp, fp, vp]
     L.echo_mlp_train.argtypes = [vp, vp, C.c_long, C.POINTER(TrainCfg), fp, fp, vp]
     L.echo_mlp_harvest.argtypes = [vp, ip, C.c_long, vp, vp, C.c_long, C.POINTER(C.c_long)]
+    L.echo_mlp_guess.argtypes = [vp, vp, ip]
     L.echo_decomp_min_halo.argtypes = [C.POINTER(Config)]
     L.echo_decomp_create.argtypes = [C.POINTER(Config), ip, ip, ip, ip, C.POINTER(vp)]
     L.echo_decomp_destroy.argtypes = [vp]
@@ -510,5 +512,16 @@ def _solver_mlp_harvest(self, nsteps, stride, feats, target):
     return cnt.value
 
 
+def _solver_mlp_guess(self, out=None, device=False):
+    """The learned starting guess W0 = U y of every cell for the current state
+    (echo_mlp_guess), [nz][ny][nx]."""
+    out = self._out(self.n, self.shape, device) if out is None else out
+    p, kind = _ptr(out, "out", self.n)
+    self._sync_torch(kind)
+    self._check(self.L.echo_mlp_guess(self._h, p, kind))
+    return out
+
+
 Solver.mlp_load = _solver_mlp_load
+Solver.mlp_guess = _solver_mlp_guess
 Solver.mlp_harvest = _solver_mlp_harvest

@@ -231,22 +231,41 @@ def _modes(kmax):
     return np.array(out, dtype=np.float64)
 
 
-def _synth(n, modes, coef, phase, off):
+def _synth(n, modes, coef, phase, off, device=None):
     """Real periodic field sum_m coef[m] cos(k_m . x + phase[m]) on an n^3 grid of a
     2 pi box, sampled at (i + off) h per axis (h = 2 pi / n), by inverse real FFT
-    (exact for integer wave vectors).  Returns [nz, ny, nx]."""
-    spec = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    (exact for integer wave vectors).  Returns [nz, ny, nx]: a numpy array, or a
+    float64 torch tensor on ``device`` when one is given (the same sums, for grids
+    whose synthesis would take minutes on the host)."""
     h = 2.0 * np.pi / n
+    # the nonzero spectral coefficients (index, value), accumulated on the host
+    entries = {}
+
+    def put(idx, c):
+        entries[idx] = entries.get(idx, 0.0) + c
+
     for m, k in enumerate(modes):
         kx, ky, kz = (int(round(q)) for q in k)
         shift = (kx * off[0] + ky * off[1] + kz * off[2]) * h
         c = coef[m] * np.exp(1j * (phase[m] + shift)) * n ** 3
         if kx > 0:
-            spec[kz % n, ky % n, kx] += c
+            put((kz % n, ky % n, kx), c)
         else:  # kx = 0 plane: put both members of the pair (irfftn needs Hermitian input)
-            spec[kz % n, ky % n, 0] += 0.5 * c
-            spec[(-kz) % n, (-ky) % n, 0] += 0.5 * np.conj(c)
-    return np.fft.irfftn(spec, s=(n, n, n), axes=(0, 1, 2))
+            put((kz % n, ky % n, 0), 0.5 * c)
+            put(((-kz) % n, (-ky) % n, 0), 0.5 * np.conj(c))
+    idx = np.array(list(entries.keys()), dtype=np.int64).reshape(-1, 3)
+    val = np.array(list(entries.values()), dtype=np.complex128)
+    if device is None:
+        spec = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+        spec[idx[:, 0], idx[:, 1], idx[:, 2]] = val
+        return np.fft.irfftn(spec, s=(n, n, n), axes=(0, 1, 2))
+    import torch
+    spec = torch.zeros((n, n, n // 2 + 1), dtype=torch.complex128, device=device)
+    ti = torch.from_numpy(idx).to(device)
+    spec[ti[:, 0], ti[:, 1], ti[:, 2]] = torch.from_numpy(val).to(device)
+    out = torch.fft.irfftn(spec, s=(n, n, n), dim=(0, 1, 2))
+    del spec
+    return out
 
 
 class Turbulence:
@@ -266,8 +285,9 @@ class Turbulence:
     factor on the grid is lorentz_max.  Seeded (PCG64)."""
 
     def __init__(self, n, seed, sigma0=10.0, beta0=1.0, rho0=1.0, eta_b=0.5, lorentz_max=5.0,
-                 kmax=4.0, gam=GAMMA):
+                 kmax=4.0, gam=GAMMA, device=None):
         self.n = n
+        self.device = device  # None: numpy arrays; else float64 torch tensors there
         self.L = (2 * np.pi,) * 3
         self.rho0, self.gam = rho0, gam
         self.B0 = math.sqrt(sigma0 * rho0)
@@ -291,18 +311,44 @@ class Turbulence:
         self._kn = kn
         # unit-amplitude delta B and u at cell centres, for the normalisation
         c = (0.5, 0.5, 0.5)
-        dB = np.array([_synth(n, self.modes, kxe_B[:, q], self.phB, c) for q in range(3)])
-        self.aB = eta_b * self.B0 / np.mean(np.sqrt(np.sum(dB ** 2, axis=0)))
-        self._dBc = dB * self.aB
-        u = np.array([_synth(n, self.modes, kxe_u[:, q], self.phu, c) for q in range(3)])
-        umax = np.max(np.sqrt(np.sum(u ** 2, axis=0)))
-        self.au = math.sqrt(lorentz_max ** 2 - 1.0) / umax
-        u *= self.au
-        self._v = u / np.sqrt(1.0 + np.sum(u ** 2, axis=0))[None]
+        if device is None:
+            dB = np.array([_synth(n, self.modes, kxe_B[:, q], self.phB, c) for q in range(3)])
+            self.aB = eta_b * self.B0 / np.mean(np.sqrt(np.sum(dB ** 2, axis=0)))
+            self._dBc = dB * self.aB
+            u = np.array([_synth(n, self.modes, kxe_u[:, q], self.phu, c) for q in range(3)])
+            umax = np.max(np.sqrt(np.sum(u ** 2, axis=0)))
+            self.au = math.sqrt(lorentz_max ** 2 - 1.0) / umax
+            u *= self.au
+            self._v = u / np.sqrt(1.0 + np.sum(u ** 2, axis=0))[None]
+        else:
+            import torch
+            m2 = None
+            for q in range(3):
+                f = _synth(n, self.modes, kxe_B[:, q], self.phB, c, device)
+                m2 = f * f if m2 is None else m2.add_(f * f)
+                del f
+            self.aB = eta_b * self.B0 / float(torch.sqrt(m2).mean())
+            del m2
+            self._dBc = None  # the cell-centred field is only needed without UCT
+            u = torch.stack([_synth(n, self.modes, kxe_u[:, q], self.phu, c, device)
+                             for q in range(3)])
+            u2 = (u * u).sum(0)
+            umax = float(torch.sqrt(u2.max()))
+            self.au = math.sqrt(lorentz_max ** 2 - 1.0) / umax
+            u *= self.au
+            u2 *= self.au ** 2
+            self._v = u.div_(torch.sqrt(1.0 + u2)[None])
+            del u2
+
+    def _empty(self, shape):
+        if self.device is None:
+            return np.empty(shape)
+        import torch
+        return torch.empty(shape, dtype=torch.float64, device=self.device)
 
     def prim5(self):
         n = self.n
-        out = np.empty((5, n, n, n))
+        out = self._empty((5, n, n, n))
         out[0] = self.rho0
         out[1:4] = self._v
         out[4] = self.p0
@@ -310,7 +356,8 @@ class Turbulence:
 
     def bface_background(self):
         n = self.n
-        out = np.zeros((3, n, n, n))
+        out = self._empty((3, n, n, n))
+        out[0:2] = 0.0
         out[2] = self.B0
         return out
 
@@ -325,12 +372,16 @@ class Turbulence:
         """Edge vector potential: A_x at (i, j+1/2, k+1/2) and cyclic."""
         n = self.n
         offs = [(0.5, 1.0, 1.0), (1.0, 0.5, 1.0), (1.0, 1.0, 0.5)]
-        out = np.empty((3, n, n, n))
+        out = self._empty((3, n, n, n))
         for c in range(3):
             # sin(k.x + phi) = cos(k.x + phi - pi/2)
             coef = self.aB / self._kn * self.eB[:, c]
-            out[c] = _synth(n, self.modes, coef, self.phB - 0.5 * np.pi, offs[c])
+            out[c] = _synth(n, self.modes, coef, self.phB - 0.5 * np.pi, offs[c], self.device)
         return out
+
+    def release(self):
+        """Drop the stored velocity field (after prim5() has been taken)."""
+        self._v = None
 
 
 # ---------------------------------------------------------------------------

@@ -110,3 +110,167 @@ def test_turbulence_parity_with_oracle():
     g.step(5)
     s.step(5)
     assert_parity(s.primitives(), g.primitives(), PRIM_GROUPS, what="turbulence 24^3")
+
+
+def _fp32_features(u, B):
+    """The oracle's features of the states the GPU sees, rounded to float32 (the
+    GPU forms them in float32 from the rounded components)."""
+    return mlp.features(u, B).astype(np.float32).astype(np.float64)
+
+
+def test_harvest_matches_oracle_features_and_targets():
+    """echo_mlp_harvest with stride 1 returns, in cell order, the features of every
+    cell and its converged W/U after each inversion.  Stage 1 inverts the initial
+    state and stage 2 the state after the first stage update; both are compared
+    with the oracle's features (oracle/mlp.features of its own state and INT field)
+    and its converged W/U, within float32 rounding."""
+    import torch
+    n = (20, 12, 9)
+    ncell = int(np.prod(n))
+    L = (1.0, 0.8, 0.6)
+    st = wl.random_smooth_fields(*n, seed=107, amp=0.6, L=L)
+    s = echo.Solver(*n, L=L)
+    s.set_state(*st)
+    cap = 3 * ncell
+    feats = torch.empty((cap, 5), dtype=torch.float32, device="cuda")
+    target = torch.empty(cap, dtype=torch.float32, device="cuda")
+    assert s.mlp_harvest(1, 1, feats, target) == cap
+    f = feats.cpu().numpy().astype(np.float64)
+    tg = target.cpu().numpy().astype(np.float64)
+    g = orc.Grid(*n, *L)
+    g.set_state(*st)
+    rc, rb, amax, bad, prim = g.rhs(with_prims=True)
+    assert bad == 0
+    checks = [(g.cons.reshape(5, -1).copy(), prim[5:8].reshape(3, -1).copy(), g.W.reshape(-1).copy())]
+    dt = 0.4 * min(L[q] / n[q] for q in range(3)) / amax
+    g.cons = np.ascontiguousarray(g.cons + dt * rc)
+    g.bf = np.ascontiguousarray(g.bf + dt * rb)
+    rc2, rb2, _, bad2, prim2 = g.rhs(with_prims=True)
+    assert bad2 == 0
+    checks.append((g.cons.reshape(5, -1).copy(), prim2[5:8].reshape(3, -1).copy(),
+                   g.W.reshape(-1).copy()))
+    for stage, (u, B, W) in enumerate(checks):
+        got = f[stage * ncell:(stage + 1) * ncell]
+        ref = mlp.features(u, B)
+        assert np.all(np.abs(got - ref) <= 2e-6 * np.maximum(1.0, np.abs(ref))), stage
+        assert np.all(np.abs(got[:, 3] - ref[:, 3]) <= 1e-5), stage
+        tref = W / u[4]
+        assert np.allclose(tg[stage * ncell:(stage + 1) * ncell], tref, rtol=2e-7, atol=0), stage
+
+
+def _trained_weights(n=32, seed=108, steps=6):
+    """A network trained on the GPU on states harvested from a turbulence run."""
+    import torch
+    tb = wl.Turbulence(n, seed=seed, lorentz_max=3.0)
+    L = (2 * np.pi,) * 3
+    h = echo.Solver(n, n, n, L=L)
+    h.set_state(tb.prim5(), tb.bface_background(), tb.apot())
+    cap = steps * 3 * n ** 3 // 2
+    feats = torch.empty((cap, 5), dtype=torch.float32, device="cuda")
+    target = torch.empty(cap, dtype=torch.float32, device="cuda")
+    cnt = h.mlp_harvest(steps, 2, feats, target)
+    h.close()
+    w, hist = echo.mlp_train(feats[:cnt].contiguous(), target[:cnt].contiguous(),
+                             wl.mlp_init(seed + 1), epochs=6, batch=1024, lr=3e-3, lr_decay=0.7)
+    return w
+
+
+def test_in_step_guess_matches_oracle():
+    """The learned guess the inversion starts from, W0 = U y: echo_mlp_guess (the
+    device feature map and the tensor-core network) against U times the oracle's
+    forward pass on the oracle's features, within the hardware-tanh bound; then one
+    right-hand-side evaluation with the network selected against the oracle run
+    with exactly these guesses as its caller array: the same Newton iterations and
+    the same rejected guesses, so the guess computed inside the inversion kernel is
+    the one echo_mlp_guess returns."""
+    w = _trained_weights()
+    n = (24, 24, 24)
+    L = (2 * np.pi,) * 3
+    tb = wl.Turbulence(24, seed=109, lorentz_max=3.0)
+    st = (tb.prim5(), tb.bface_background(), tb.apot())
+    s = echo.Solver(*n, L=L, guess="mlp")
+    s.mlp_load(w)
+    s.set_state(*st)
+    w0 = s.mlp_guess()
+    g = orc.Grid(*n, *L)
+    g.set_state(*st)
+    _, _, _, _, prim = g.rhs(with_prims=True)   # the INT field of the state
+    u = g.cons.reshape(5, -1)
+    x = _fp32_features(u, prim[5:8].reshape(3, -1))
+    y, _ = mlp.forward(w.astype(np.float64), x, bf=True)
+    bound = np.sum(np.abs(mlp.unpack(w.astype(np.float64))["w3"])) * 2.0 ** -10 + 2e-3
+    assert np.all(np.abs(w0.reshape(-1) - u[4] * y) <= u[4] * bound + 1e-6 * np.abs(w0.reshape(-1)))
+    # the oracle from the same state with these guesses
+    g2 = orc.Grid(*n, *L, guess=orc.GUESS_ARRAY)
+    g2.set_state(*st)
+    g2.guessarr = np.ascontiguousarray(w0)
+    rc, rb, amax, bad = g2.rhs()
+    s.diagnostics(reset=True)
+    grc, grb, gamax = s.rhs()
+    d = s.diagnostics()
+    assert d["c2p_calls"] == g2.stats.cells
+    assert round(d["newton_it_mean"] * d["c2p_calls"]) == g2.stats.iters
+    assert d["c2p_fallbacks"] == g2.stats.fallbacks
+    assert gamax == pytest.approx(amax, rel=1e-13)
+
+
+def test_adam_steps_match_oracle():
+    """Training on one batch of 64 states: each epoch is one Adam step.  The GPU's
+    parameters after one and after two steps equal the oracle's Adam update
+    (oracle/mlp.adam_step, pinned by a hand-computed case) applied to the GPU's own
+    gradient at the previous parameters, to float32 rounding."""
+    import torch
+    x, t = _samples(64, 65)
+    xf = torch.from_numpy(x.astype(np.float32)).cuda()
+    tf = torch.from_numpy(t.astype(np.float32)).cuda()
+    w0 = wl.mlp_init(66)
+    lr = 1e-2
+    w1, _ = echo.mlp_train(xf, tf, w0, epochs=1, batch=64, lr=lr, lr_decay=1.0)
+    w2, _ = echo.mlp_train(xf, tf, w0, epochs=2, batch=64, lr=lr, lr_decay=1.0)
+    _, g0 = echo.mlp_grad(w0, xf, tf)
+    ref1, m1, v1 = mlp.adam_step(w0.astype(np.float64), g0, np.zeros(mlp.NPARAM),
+                                 np.zeros(mlp.NPARAM), 1, lr)
+    assert np.max(np.abs(w1 - ref1)) < 1e-6
+    # each parameter moved by about lr on the first step (mhat / sqrt(vhat) = sign g)
+    moved = np.abs(w1 - w0)[np.abs(g0) > 1e-6]
+    assert np.all(np.abs(moved - lr) < 1e-4)
+    _, g1 = echo.mlp_grad(w1, xf, tf)
+    ref2, _, _ = mlp.adam_step(w1.astype(np.float64), g1, m1, v1, 2, lr)
+    assert np.max(np.abs(w2 - ref2)) < 2e-6
+
+
+def test_learned_guess_pays_on_a_resume_without_w():
+    """A checkpoint resumed without its Newton guess W has no previous solution: the
+    method without the network starts every cell's first inversion from W0 = U.
+    With a trained network loaded, that inversion starts from the learned guess
+    instead: fewer Newton iterations for the resumed step, and the same primitives
+    (the iteration runs to tolerance either way)."""
+    w = _trained_weights()
+    n = 96
+    tb = wl.Turbulence(n, seed=110, lorentz_max=3.0)
+    L = (2 * np.pi,) * 3
+    a = echo.Solver(n, n, n, L=L)
+    a.set_state(tb.prim5(), tb.bface_background(), tb.apot())
+    a.step(2)
+    cons, bf, _, t, step = a.get_state()
+    res = {}
+    for name in ("cold", "learned"):
+        r = echo.Solver(n, n, n, L=L)
+        if name == "learned":
+            r.mlp_load(w)
+        times = []
+        for rep in range(3):
+            r.set_conserved(cons, bf, None, t, step)
+            r.diagnostics(reset=True)
+            r.profile(True)
+            r.profile_read(reset=True)
+            r.step(1)
+            prof = r.profile_read(reset=True)
+            r.profile(False)
+            times.append(prof["int_c2p"][1])
+        d = r.diagnostics()
+        res[name] = (min(times), d["newton_it_mean"], d["c2p_fallbacks"], r.primitives())
+        r.close()
+    assert res["learned"][1] < res["cold"][1], {k: v[:3] for k, v in res.items()}
+    assert res["learned"][2] < 0.01 * 3 * n ** 3
+    assert_parity(res["learned"][3], res["cold"][3], PRIM_GROUPS, what="learned vs cold restart")

@@ -77,7 +77,10 @@ def test_primitives_parity():
 
 
 def test_steps_parity_alfven_32():
-    """The 32^3 Alfven wave along x, FP64, 20 SSP-RK3 steps at CFL 0.4."""
+    """The 32^3 Alfven wave along x, FP64, 20 SSP-RK3 steps at CFL 0.4.  The GPU runs
+    the library's Newton tolerance (1e-6 with the polishing step); the oracle is run
+    twice, with that tolerance and with 1e-12, so the inversion's result is checked
+    against a tighter solve too, not only against the same stopping rule."""
     n = (32, 32, 32)
     c, st = cpa_state(n, (1, 0, 0))
     g, s = make_pair(n, state=st)
@@ -90,6 +93,12 @@ def test_steps_parity_alfven_32():
     assert step == 20
     assert_parity(cons, g.cons, CONS_GROUPS, what="cons")
     assert_parity(bf, g.bf, FACE_GROUPS, what="bface")
+    tight = orc.Grid(*n, tol=1e-12)
+    tight.set_state(*st)
+    tight.step(20)
+    assert tight.t == pytest.approx(g.t, rel=1e-13)
+    assert_parity(s.primitives(), tight.primitives(), PRIM_GROUPS, what="vs oracle at tol 1e-12")
+    assert_parity(cons, tight.cons, CONS_GROUPS, what="cons vs oracle at tol 1e-12")
 
 
 @pytest.mark.parametrize("ho", [0, 1])
@@ -362,3 +371,59 @@ def test_turbulence_2d_parity(precision):
     b_over_h = tb.B0 * n / (2 * np.pi)
     assert d["divb_max"] < (1e-11 if precision == "fp64" else 1e-7) * b_over_h
     assert d["c2p_failures"] == 0
+
+
+def _oracle_view(n, L, ho, cons, bf):
+    """An oracle grid holding a given state (for its totals and div B)."""
+    g = orc.Grid(*n, *L, ho=ho)
+    g.cons = np.ascontiguousarray(cons)
+    g.bf = np.ascontiguousarray(bf)
+    return g
+
+
+@pytest.mark.parametrize("ho", [0, 1])
+def test_diagnostics_match_oracle(ho):
+    """echo_diagnostics against the oracle on the same states (Sec. 3: UCT keeps the
+    discrete div B at round-off; the periodic box conserves the totals):
+      - after 3 steps of both, the Newton statistics (calls, summed iterations,
+        largest count) equal the oracle's: same guesses, same stopping rule;
+      - the conserved totals equal orc_totals of the GPU's state to rounding;
+      - on a face field that is not solenoidal (div B of order |B|/h), max |div B|
+        and its RMS equal those of orc_divb, which checks the stencil, the divisor
+        and the RMS normalisation;
+      - a non-finite value planted in the state is counted."""
+    n, L = (40, 24, 20), (1.0, 0.8, 0.6)
+    g, s = make_pair(n, L=L, ho=ho, state=smooth(n, 38, L=L))
+    assert g.step(3) == 0
+    s.step(3)
+    d = s.diagnostics()
+    ncell = int(np.prod(n))
+    assert d["c2p_calls"] == g.stats.cells == 9 * ncell
+    assert round(d["newton_it_mean"] * d["c2p_calls"]) == g.stats.iters
+    assert d["newton_it_max"] == g.stats.itmax
+    assert d["c2p_failures"] == g.stats.failures == 0
+    cons, bf, w, t, step = s.get_state()
+    ref = _oracle_view(n, L, ho, cons, bf)
+    tot = ref.totals()
+    scale = np.abs(cons).sum(axis=(1, 2, 3)).max()
+    assert np.max(np.abs(np.array(d["tot"]) - tot)) <= 1e-13 * scale
+    # div B of the stepped state is round-off on both sides
+    h = min(L[q] / n[q] for q in range(3))
+    assert d["divb_max"] <= 1e-12 * np.abs(bf).max() / h
+    assert np.max(np.abs(ref.divb())) <= 1e-12 * np.abs(bf).max() / h
+    # a face field with a divergence
+    rng = np.random.default_rng(39)
+    bfr = bf + 0.1 * rng.standard_normal(bf.shape)
+    s.set_conserved(cons, bfr, w, t, step)
+    d2 = s.diagnostics()
+    div = _oracle_view(n, L, ho, cons, bfr).divb()
+    assert np.max(np.abs(div)) > 1.0
+    assert d2["divb_max"] == pytest.approx(np.max(np.abs(div)), rel=1e-12)
+    assert d2["divb_l2"] == pytest.approx(np.sqrt(np.mean(div * div)), rel=1e-12)
+    face_tot = _oracle_view(n, L, ho, cons, bfr).totals()[5:]
+    assert np.max(np.abs(np.array(d2["tot"][5:]) - face_tot)) <= 1e-13 * np.abs(bfr).sum()
+    assert d2["nonfinite"] == 0
+    bad = cons.copy()
+    bad[2, 5, 6, 7] = np.nan
+    s.set_conserved(bad, bfr, w, t, step)
+    assert s.diagnostics()["nonfinite"] == 1

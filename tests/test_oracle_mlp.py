@@ -67,3 +67,25 @@ def test_bf16_emulation_is_close_to_fp64():
     lbf, gbf = mlp.loss_grad(theta, x, t, bf=True)
     assert abs(lbf - l64) / l64 < 1e-2
     assert np.linalg.norm(gbf - g64) / np.linalg.norm(g64) < 2e-2
+
+
+def test_adam_step_hand_computed():
+    """Two Adam steps on three parameters, worked by hand (lr 0.01, beta1 0.9,
+    beta2 0.999, eps 1e-8).  Step 1, g = (0.1, -0.2, 0): m = 0.1 g, v = 0.001 g^2,
+    so the bias-corrected mhat = g and vhat = g^2, and each parameter moves by
+    lr g / (|g| + eps): 0.01 * 0.1 / 0.10000001 = 0.0099999990000001 and
+    0.01 * 0.2 / 0.20000001 = 0.0099999995; the parameter with g = 0 stays.
+    Step 2, g = (0.05, 0.1, -0.3): m = (0.014, -0.008, -0.03),
+    v = (1.249e-5, 4.996e-5, 9.0e-5); mhat = m / 0.19 = (0.0736842105, -0.0421052632,
+    -0.1578947368), vhat = v / 0.001999 = (0.0062481241, 0.0249924962,
+    0.0450225113); the updates lr mhat / (sqrt(vhat) + eps) give the values below
+    (decimal arithmetic to 30 digits)."""
+    theta = np.array([1.0, 2.0, 3.0])
+    m = v = np.zeros(3)
+    theta, m, v = mlp.adam_step(theta, [0.1, -0.2, 0.0], m, v, 1, 0.01)
+    assert np.allclose(m, [0.01, -0.02, 0.0], rtol=1e-14, atol=0)
+    assert np.allclose(v, [1e-5, 4e-5, 0.0], rtol=1e-14, atol=0)
+    assert np.allclose(theta, [0.9900000009999999, 2.0099999995, 3.0], rtol=1e-15, atol=0)
+    theta, m, v = mlp.adam_step(theta, [0.05, 0.1, -0.3], m, v, 2, 0.01)
+    assert np.allclose(theta, [0.9806782057911869, 2.0126633697281324, 3.0074413678849681],
+                       rtol=1e-14, atol=0)

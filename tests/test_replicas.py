@@ -53,7 +53,7 @@ def test_job_rate_single_rank():
 def _reference(env_rank):
     env = dict(os.environ, RANK=str(env_rank), WORLD_SIZE="2", LOCAL_RANK=str(env_rank))
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                           "--steps", "1", "--warmup", "0", "--ref-n", "8"],
+                           "--steps", "1", "--warmup", "0", "--ref-n", "8", "--workload", "wave"],
                           capture_output=True, text=True, env=env, timeout=300)
 
 
