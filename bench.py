@@ -284,7 +284,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", type=int, default=1, help="also time mixed and mixed+learned")
     ap.add_argument("--train-n", type=int, default=128)
-    ap.add_argument("--train-steps", type=int, default=20)
+    ap.add_argument("--train-steps", type=int, default=12)
     ap.add_argument("--config", type=int, default=0,
                     help="1..5: benchmark-plan configurations; 6: the 2.5-D turbulence run of "
                          "Sec. 5; 7: 2 x 2 x 2 blocks with the wide halo against one grid")
@@ -482,11 +482,11 @@ def harvest_and_train(n_h, steps, stride, make_state, L, seed, epochs=4, cap=Non
 
 def train_guess(args):
     """The network of the learned guess for the selected workload: about 1e7 states
-    harvested (every 4th cell after every inversion) from a --train-n^3 run of another
-    seed of the same workload, trained on the GPU."""
+    harvested (every 8th cell after every inversion of --train-steps steps) from a
+    --train-n^3 run of another seed of the same workload, trained on the GPU."""
     if args.workload == "turbulence":
         mk = lambda m: turbulence_state(m, args.lorentz_max, seed=SEED + 1)
-        return harvest_and_train(args.train_n, args.train_steps, 4, mk, TURB_L, SEED + 2,
+        return harvest_and_train(args.train_n, args.train_steps, 8, mk, TURB_L, SEED + 2,
                                  cap=10_000_000)
     mk = lambda m: workload_state(m, args.wave)[1]
     return harvest_and_train(64, 8, 4, mk, (1.0, 1.0, 1.0), SEED + 2)

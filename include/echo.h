@@ -226,8 +226,8 @@ echo_status echo_mlp_load(echo_ctx *ctx, const float *weights, long n);
 
 /* The learned guess W0 = U y of every cell for the current state, out [nz][ny][nx]
  * (host or device, ptr_kind): the value the inversion starts from when it uses the
- * network (the same device code, rounded through float).  ECHO_ERR_STATE before
- * echo_mlp_load or echo_set_state; allocates n floats on the first call. */
+ * network (the same device code).  ECHO_ERR_STATE before echo_mlp_load or
+ * echo_set_state; allocates n doubles on the first call. */
 echo_status echo_mlp_guess(echo_ctx *ctx, double *out, int ptr_kind);
 
 /* Inference on its own: y[n] (device) for features feats[n][5] (device) with the

@@ -53,6 +53,11 @@ def features(u, B):
     return np.stack([D / U, S2 / (U * U), B2 / U, cos2, np.log(U / D)], axis=1)
 
 
+def f16(x):
+    """Round to IEEE half precision (nearest even) and back to float64."""
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
 def forward(theta, x, bf=False):
     p = unpack(theta)
     r = bf16 if bf else (lambda a: a)
@@ -62,6 +67,40 @@ def forward(theta, x, bf=False):
     h2 = np.tanh(z2)
     y = h2 @ p["w3"] + p["b3"][0]
     return y, (x, z1, h1, z2, h2)
+
+
+def split16(a):
+    """a = hi + lo with hi the f16 rounding of a and lo the f16 rounding of the rest."""
+    hi = f16(a)
+    return hi, f16(np.asarray(a, dtype=np.float64) - hi)
+
+
+def forward_infer(theta, x):
+    """The forward pass as the GPU's inference runs it, on f16 operands with exact
+    accumulation: layer 1 from the split features and weights (x = xh + xl,
+    W1 = Wh + Wl) as xh Wh + xl Wh + xh Wl; each tanh taken on the f16-rounded
+    pre-activation and returned in f16; layer 2 on f16 W2; the output from the
+    split w3 = hi + lo; the biases exact.  Returns y and the two hidden layers."""
+    p = unpack(theta)
+    xh, xl = split16(np.asarray(x, dtype=np.float64).astype(np.float32))
+    Wh, Wl = split16(np.asarray(p["W1"]).astype(np.float32))
+    z1 = xh @ Wh.T + xl @ Wh.T + xh @ Wl.T + p["b1"]
+    h1 = f16(np.tanh(f16(z1)))
+    z2 = h1 @ f16(p["W2"]).T + p["b2"]
+    h2 = f16(np.tanh(f16(z2)))
+    wh, wl = split16(np.asarray(p["w3"]).astype(np.float32))
+    y = h2 @ wh + h2 @ wl + p["b3"][0]
+    return y, (h1, h2)
+
+
+def infer_bound(theta, ulps=2.0):
+    """Per-sample bound on |y_gpu - y_oracle| from the hardware tanh: each hidden
+    value may differ by `ulps` f16 units in the last place (2^-10 for |h| < 1) from
+    the oracle's correctly rounded one; layer 1's differences reach y through
+    |W2| and |w3|."""
+    p = unpack(theta)
+    e = ulps * 2.0 ** -11
+    return float(np.sum(np.abs(p["w3"]) * (e + e * np.sum(np.abs(p["W2"]), axis=1))))
 
 
 def loss_grad(theta, x, t, bf=False):

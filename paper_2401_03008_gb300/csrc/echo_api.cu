@@ -579,21 +579,15 @@ echo_status echo_mlp_guess(echo_ctx *c, double *out, int ptr_kind)
     if (st) return st;
     const long n = c->g.n;
     if (!c->guess) {
-        if (cudaMalloc((void **)&c->guess, n * sizeof(float)) != cudaSuccess) {
+        if (cudaMalloc((void **)&c->guess, n * sizeof(double)) != cudaSuccess) {
             c->guess = nullptr;
             cudaGetLastError();
-            return fail(c, ECHO_ERR_OOM, "echo_mlp_guess: %ld floats do not fit", n);
+            return fail(c, ECHO_ERR_OOM, "echo_mlp_guess: %ld doubles do not fit", n);
         }
-    }
-    double *d = out;
-    if (ptr_kind != ECHO_PTR_DEVICE) {
-        if ((st = ensure_stage(c))) return st;
-        d = c->stage8;
     }
     if (c->mixed) Path<float>::mlp_guess(c);
     else Path<double>::mlp_guess(c);
-    echo::launch_widen(c, d, c->guess, n);
-    if ((st = output(c, out, d, n, ptr_kind))) return st;
+    if ((st = output(c, out, c->guess, n, ptr_kind))) return st;
     return sync_check(c);
 }
 

@@ -557,10 +557,9 @@ __device__ __forceinline__ double c2p_pre32(const C2PInv &q, double W0, int &ite
 // point computes v^2 and 1/(W (W+B^2)) there, and the next iteration reuses both,
 // so an iteration costs two divisions and one reciprocal square root.
 // Returns true on success.  prim = (rho, vx, vy, vz, p); B the cell-centred field.
-__device__ __forceinline__ bool c2p_newton(const double *u, const double *B, double gm1g,
-                                           float gm1g32, double W0, double tol, int maxit,
-                                           double *prim, double &Wout, int &iters, int pre32,
-                                           int &iters32)
+// the invariants D, S^2, B^2, S.B, U of a cell's conserved state and field
+__device__ __forceinline__ C2PInv c2p_invariants(const double *u, const double *B, double gm1g,
+                                                 float gm1g32)
 {
     C2PInv q;
     q.D = u[0];
@@ -570,6 +569,17 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     q.U = u[4];
     q.gm1g = gm1g;  // (gam - 1)/gam, formed once on the host
     q.gm1g32 = gm1g32;
+    return q;
+}
+
+// Wfb: a second starting point, taken when W0 lies outside the domain (the
+// previous W when W0 is the learned guess; *fb reports that it was taken); pass
+// fb = nullptr for none.
+__device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, const double *B,
+                                           double W0, double tol, int maxit, double *prim,
+                                           double &Wout, int &iters, int pre32, int &iters32,
+                                           double Wfb = 0.0, bool *fb = nullptr)
+{
     const double SB2 = q.SB * q.SB;
     iters32 = 0;
     // mixed path: FP32 iterations first; their last derivative then serves every
@@ -581,6 +591,13 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     const double idf = to_f64(idf32);
     double W = W0, v2 = 0.0, r = 0.0;
     bool ok = c2p_eval(q, W, v2, r);
+    if (fb) {
+        *fb = !ok;
+        if (!ok) {
+            W = Wfb;
+            ok = c2p_eval(q, W, v2, r);
+        }
+    }
     for (int k = 0; k < 64 && !ok; k++) {
         W = (gtz(W) && finite64(W)) ? 2.0 * W : fabs(q.U) + 1.0;
         ok = c2p_eval(q, W, v2, r);
@@ -652,6 +669,15 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
     prim[0] = rho;
     prim[4] = p;
     return ok && conv && finite64(p) && finite64(rho) && gtz(p) && gtz(rho) && lt(v2, 1.0);
+}
+
+__device__ __forceinline__ bool c2p_newton(const double *u, const double *B, double gm1g,
+                                           float gm1g32, double W0, double tol, int maxit,
+                                           double *prim, double &Wout, int &iters, int pre32,
+                                           int &iters32)
+{
+    const C2PInv q = c2p_invariants(u, B, gm1g, gm1g32);
+    return c2p_newton(q, u, B, W0, tol, maxit, prim, Wout, iters, pre32, iters32);
 }
 
 // ---------------------------------------------------------------------------

@@ -45,7 +45,7 @@ struct echo_ctx {
     double *dres;           // reduction results (device)
     double *stage8;         // staging for host outputs [8][n] (allocated on demand)
     void *mlp_w;            // learned-guess weights in their device form, or NULL
-    float *guess;           // learned guesses [n] for echo_mlp_guess (allocated on demand)
+    double *guess;          // learned guesses [n] for echo_mlp_guess (allocated on demand)
     // W holds no previous solution (a checkpoint resumed without it: W = U); the
     // next inversion starts from the learned guess if the weights are loaded
     bool w_cold;
@@ -138,8 +138,6 @@ void launch_diag_mode(echo_ctx *c, int mode, const double *a, const double *b);
 void launch_copy_state(echo_ctx *c, double *dst_u, double *dst_b, const double *src_u,
                        const double *src_b);
 void launch_w_from_cold(echo_ctx *c);
-// out[q] = in[q] widened to double, q < m
-void launch_widen(echo_ctx *c, double *out, const float *in, long m);
 // refresh the float copy of the face field (mixed path) after the state changed
 void launch_bf32(echo_ctx *c);
 double probe_fma_peak(echo_ctx *c, int fp64);

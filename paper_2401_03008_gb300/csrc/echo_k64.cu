@@ -102,17 +102,6 @@ void launch_bf32(echo_ctx *c)
     launch(c, K_MISC, k_to_float, nblocks(m, BS), BS, 0, m, (const double *)c->Bf, c->Bf32);
 }
 
-__global__ void __launch_bounds__(BS) k_widen(long m, const float *__restrict__ in, double *__restrict__ out)
-{
-    long q = blockIdx.x * (long)BS + threadIdx.x;
-    if (q < m) out[q] = to_f64(in[q]);
-}
-
-void launch_widen(echo_ctx *c, double *out, const float *in, long m)
-{
-    launch(c, K_MISC, k_widen, nblocks(m, BS), BS, 0, m, in, out);
-}
-
 // cold guess W0 = U for a resumed state without a stored guess
 __global__ void __launch_bounds__(BS) k_w_cold(long n, const double *__restrict__ U, double *__restrict__ W)
 {

@@ -97,8 +97,13 @@ __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
 // through L1); a guess that is unusable falls back to the previous W and is counted.
 // The network runs on whole warps, before the divergent Newton iteration: lanes
 // past the grid evaluate it on a placeholder state.
+// The network variant asks for the same three blocks on the FP64 path (the cell's
+// state is spilled across the network and reloaded, cheaper than a block less);
+// the FP32 path takes two blocks rather than spill more.
+constexpr int minb_c2p_mlp(int rbytes) { return rbytes == 4 ? 2 : 3; }
+
 template <typename R, bool MLP>
-__global__ void __launch_bounds__(BS, MLP ? 2 : minb_c2p(sizeof(R)))
+__global__ void __launch_bounds__(BS, MLP ? minb_c2p_mlp(sizeof(R)) : minb_c2p(sizeof(R)))
 k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
           double *__restrict__ W, const MlpDev *__restrict__ mw, R *__restrict__ prim,
           C2PParams par, DevScalars *sc, int stage, int update_w, int count)
@@ -120,30 +125,29 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
 #pragma unroll
         for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
     }
-    double Wml = 0.0;
-    if (MLP) Wml = mlp_guess_warp(*mw, u, B, threadIdx.x & 31);
+    // the invariants serve the learned guess's features and the Newton iteration
+    const C2PInv q = c2p_invariants(u, B, g.gm1g, g.gm1g32);
+    double W0 = 0.0;
+    if (MLP) {
+        W0 = mlp_guess_warp(*mw, q, threadIdx.x & 31);
+        // the conserved state is read again (from L1) rather than held in registers
+        // across the network, whose fragments need them
+        asm volatile("" ::: "memory");
+        if (active)
+#pragma unroll
+            for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
+    }
     if (active) {
-        double W0;
-        if (MLP) {
-            W0 = Wml;
-            C2PInv q;
-            q.D = u[0];
-            q.S2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
-            q.B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-            q.SB = u[1] * B[0] + u[2] * B[1] + u[3] * B[2];
-            q.U = u[4];
-            if (!c2p_ok(q, W0)) {
-                W0 = W[c];
-                fb = true;
-            }
-        } else if (par.guess == 1) {
-            W0 = u[4];
-        } else {
-            W0 = W[c];
-        }
+        // an unusable learned guess (outside W > 0, v^2 < 1) falls back to the previous
+        // W inside the Newton routine's first evaluation, and is counted
+        double Wfb = 0.0;
+        if (MLP) Wfb = W[c];
+        else if (par.guess == 1) W0 = u[4];
+        else W0 = W[c];
         double p[5], Wn;
         int iters, iters32;
-        bad = !c2p_newton(u, B, g.gm1g, g.gm1g32, W0, par.tol, par.maxit, p, Wn, iters, par.pre32, iters32);
+        bad = !c2p_newton(q, u, B, W0, par.tol, par.maxit, p, Wn, iters, par.pre32, iters32, Wfb,
+                          MLP ? &fb : nullptr);
         it = (unsigned)iters;
         it32 = (unsigned)iters32;
 #pragma unroll
@@ -188,7 +192,7 @@ constexpr int MLP_BS = 128;
 template <typename BT>
 __global__ void __launch_bounds__(MLP_BS)
 k_mlp_guess(Grid g, const double *__restrict__ U, const BT *__restrict__ Bf,
-            const MlpDev *__restrict__ w, float *__restrict__ guess)
+            const MlpDev *__restrict__ w, double *__restrict__ guess)
 {
     __shared__ __align__(16) unsigned char smem[MLP_INFER_BYTES];
     const MlpDev &sw = load_mlp_shared(smem, w);
@@ -203,8 +207,8 @@ k_mlp_guess(Grid g, const double *__restrict__ U, const BT *__restrict__ Bf,
             for (int d = 0; d < 3; d++) B[d] = cell_field(g, Bf, c, i, j, k, d);
             for (int v = 0; v < 5; v++) u[v] = U[v * n + c];
         }
-        const double w0 = mlp_guess_warp(sw, u, B, lane);
-        if (c < n) guess[c] = to_f32(w0);
+        const double w0 = mlp_guess_warp(sw, c2p_invariants(u, B, g.gm1g, g.gm1g32), lane);
+        if (c < n) guess[c] = w0;
     }
 }
 

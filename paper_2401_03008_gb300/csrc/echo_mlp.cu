@@ -40,6 +40,12 @@ k_mlp_forward(long n, const float *__restrict__ feats, const MlpDev *__restrict_
 }
 
 // build the device form from the flat FP32 parameters
+__device__ __forceinline__ unsigned h2pair(float lo, float hi)
+{
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
 __global__ void k_mlp_build(const float *__restrict__ p, MlpDev *w)
 {
     for (int q = threadIdx.x; q < NH * NH; q += blockDim.x) {
@@ -50,7 +56,32 @@ __global__ void k_mlp_build(const float *__restrict__ p, MlpDev *w)
     for (int q = threadIdx.x; q < (NH / 8) * (NH / 16) * 32; q += blockDim.x) {
         const int nt = q / 128, kk = (q / 32) % 4, lane = q % 32, g = lane >> 2, t = lane & 3;
         const float *row = p + O_W2 + (8 * nt + g) * NH + 16 * kk + 2 * t;
-        w->W2F[nt][kk][lane] = make_uint2(pack_bf16(row[0], row[1]), pack_bf16(row[8], row[9]));
+        w->W2H[nt][kk][lane] = make_uint2(h2pair(row[0], row[1]), h2pair(row[8], row[9]));
+    }
+    // f16 split v = hi + lo of a weight
+    auto hi16 = [](float v) { return __half2float(__float2half_rn(v)); };
+    for (int q = threadIdx.x; q < (NH / 8) * 32; q += blockDim.x) {
+        const int j = q / 32, lane = q % 32, g = lane >> 2, t = lane & 3;
+        const float *row = p + O_W1 + (8 * j + g) * NIN;
+        // k column c of the stacked (Whi, Whi, Wlo, 0)
+        auto colv = [&](int c) -> float {
+            if (c < NIN) return hi16(row[c]);
+            if (c < 2 * NIN) return hi16(row[c - NIN]);
+            if (c < 3 * NIN) return row[c - 2 * NIN] - hi16(row[c - 2 * NIN]);
+            return 0.f;
+        };
+        w->W1H[j][lane] = make_uint2(h2pair(colv(2 * t), colv(2 * t + 1)),
+                                     h2pair(colv(2 * t + 8), colv(2 * t + 9)));
+    }
+    for (int q = threadIdx.x; q < (NH / 16) * 32; q += blockDim.x) {
+        const int kk = q / 32, lane = q % 32, g = lane >> 2, t = lane & 3;
+        const float *v = p + O_W3 + 16 * kk + 2 * t;
+        uint2 f = make_uint2(0u, 0u);
+        if (g == 0) f = make_uint2(h2pair(hi16(v[0]), hi16(v[1])), h2pair(hi16(v[8]), hi16(v[9])));
+        if (g == 1)
+            f = make_uint2(h2pair(v[0] - hi16(v[0]), v[1] - hi16(v[1])),
+                           h2pair(v[8] - hi16(v[8]), v[9] - hi16(v[9])));
+        w->W3H[kk][lane] = f;
     }
     for (int q = threadIdx.x; q < NH * NIN; q += blockDim.x) w->W1[q] = p[O_W1 + q];
     for (int q = threadIdx.x; q < NH; q += blockDim.x) {

@@ -23,20 +23,23 @@ def _samples(n, seed):
 
 
 def test_forward_matches_oracle():
+    """Tensor-core inference (f16 operands, FP32 accumulation, hardware tanh on f16
+    pairs) against the oracle's forward pass rounded at the same points: every
+    sample within the worst-case bound of the hardware tanh's error, the mean error
+    well inside it (a wrong fragment mapping or layer would be off by O(0.1) on
+    most samples); and close to the exact FP64 network."""
     import torch
     x, t = _samples(1000, 61)  # not a multiple of 32: ragged last warp
-    w = wl.mlp_init(62)
-    y = echo.mlp_forward(w, torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
-    # the oracle gets the features the GPU saw (float32) and rounds at the same points.
-    # Inference uses the hardware tanh (absolute error about 2^-11 per activation):
-    # through the 64 x 64 layer and the output dot product that stays below
-    # sum |w3| * 2^-10 plus a bf16 rounding flip or two of the hidden layer
-    ref, _ = mlp.forward(w.astype(np.float64), x.astype(np.float32).astype(np.float64), bf=True)
-    p = mlp.unpack(w.astype(np.float64))
-    bound = np.sum(np.abs(p["w3"])) * 2.0 ** -10 + 2e-3
-    assert np.max(np.abs(y - ref)) < bound
-    ref64, _ = mlp.forward(w.astype(np.float64), x)
-    assert np.max(np.abs(y - ref64)) < 2e-2
+    for seed in (62, 67):
+        w = wl.mlp_init(seed)
+        y = echo.mlp_forward(w, torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
+        w64 = w.astype(np.float64)
+        ref, _ = mlp.forward_infer(w64, x.astype(np.float32).astype(np.float64))
+        err = np.abs(y - ref)
+        assert np.max(err) <= mlp.infer_bound(w64), (np.max(err), mlp.infer_bound(w64))
+        assert np.mean(err) <= 0.1 * mlp.infer_bound(w64), np.mean(err)
+        ref64, _ = mlp.forward(w64, x)
+        assert np.max(np.abs(y - ref64)) < 2e-2
 
 
 def test_gradient_matches_oracle():
@@ -197,9 +200,11 @@ def test_in_step_guess_matches_oracle():
     _, _, _, _, prim = g.rhs(with_prims=True)   # the INT field of the state
     u = g.cons.reshape(5, -1)
     x = _fp32_features(u, prim[5:8].reshape(3, -1))
-    y, _ = mlp.forward(w.astype(np.float64), x, bf=True)
-    bound = np.sum(np.abs(mlp.unpack(w.astype(np.float64))["w3"])) * 2.0 ** -10 + 2e-3
-    assert np.all(np.abs(w0.reshape(-1) - u[4] * y) <= u[4] * bound + 1e-6 * np.abs(w0.reshape(-1)))
+    y, _ = mlp.forward_infer(w.astype(np.float64), x)
+    bound = mlp.infer_bound(w.astype(np.float64))
+    err = np.abs(w0.reshape(-1) - u[4] * y)
+    assert np.all(err <= u[4] * bound + 1e-6 * np.abs(w0.reshape(-1)))
+    assert np.mean(err / u[4]) <= 0.1 * bound
     # the oracle from the same state with these guesses
     g2 = orc.Grid(*n, *L, guess=orc.GUESS_ARRAY)
     g2.set_state(*st)
@@ -242,35 +247,84 @@ def test_adam_steps_match_oracle():
 def test_learned_guess_pays_on_a_resume_without_w():
     """A checkpoint resumed without its Newton guess W has no previous solution: the
     method without the network starts every cell's first inversion from W0 = U.
-    With a trained network loaded, that inversion starts from the learned guess
-    instead: fewer Newton iterations for the resumed step, and the same primitives
-    (the iteration runs to tolerance either way)."""
-    w = _trained_weights()
-    n = 96
-    tb = wl.Turbulence(n, seed=110, lorentz_max=3.0)
+    With a network trained on 9.4e6 states of the same workload family (another seed)
+    loaded, that inversion starts from the learned guess instead: fewer Newton
+    iterations, less inversion time (the best of four resumes each, FP64 path), and
+    the same primitives (the iteration runs to tolerance either way)."""
+    import torch
     L = (2 * np.pi,) * 3
+
+    def turb(m, seed):
+        tb = wl.Turbulence(m, seed=seed, lorentz_max=5.0, device="cuda")
+        return (tb.prim5(), tb.bface_background(), tb.apot())
+
+    h = echo.Solver(128, 128, 128, L=L)
+    h.set_state(*turb(128, 112))
+    cap = 10_000_000
+    feats = torch.empty((cap, 5), dtype=torch.float32, device="cuda")
+    target = torch.empty(cap, dtype=torch.float32, device="cuda")
+    cnt = h.mlp_harvest(12, 8, feats, target)
+    h.close()
+    w, hist = echo.mlp_train(feats[:cnt].contiguous(), target[:cnt].contiguous(),
+                             wl.mlp_init(113), epochs=4, batch=4096, lr=3e-3, lr_decay=0.6)
+    del feats, target
+    n = 128
     a = echo.Solver(n, n, n, L=L)
-    a.set_state(tb.prim5(), tb.bface_background(), tb.apot())
-    a.step(2)
-    cons, bf, _, t, step = a.get_state()
+    a.set_state(*turb(n, 114))
+    a.step(3)
+    cons, bf, _, t, step = a.get_state(device=True)
+    a.close()
     res = {}
     for name in ("cold", "learned"):
         r = echo.Solver(n, n, n, L=L)
         if name == "learned":
             r.mlp_load(w)
-        times = []
-        for rep in range(3):
+        times, its = [], []
+        for rep in range(4):
             r.set_conserved(cons, bf, None, t, step)
             r.diagnostics(reset=True)
             r.profile(True)
             r.profile_read(reset=True)
-            r.step(1)
+            r.rhs(device=True)
             prof = r.profile_read(reset=True)
             r.profile(False)
+            d = r.diagnostics()
             times.append(prof["int_c2p"][1])
-        d = r.diagnostics()
-        res[name] = (min(times), d["newton_it_mean"], d["c2p_fallbacks"], r.primitives())
+            its.append((d["newton_it_mean"], d["c2p_fallbacks"]))
+        res[name] = (min(times), its[-1][0], its[-1][1], r.primitives())
         r.close()
-    assert res["learned"][1] < res["cold"][1], {k: v[:3] for k, v in res.items()}
-    assert res["learned"][2] < 0.01 * 3 * n ** 3
+    summary = {k: v[:3] for k, v in res.items()}
+    assert res["learned"][1] < res["cold"][1], summary
+    assert res["learned"][2] < 0.01 * n ** 3, summary
+    assert res["learned"][0] < res["cold"][0], summary
     assert_parity(res["learned"][3], res["cold"][3], PRIM_GROUPS, what="learned vs cold restart")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_turbulence_lorentz5_parity_with_oracle(precision):
+    """The benchmark's turbulence at its full amplitude (largest Lorentz factor 5,
+    sigma0 = 10) on 64^3, the coarsest grid on which the oracle's first steps run
+    clean: 5 SSP-RK3 steps, FP64 element by element at the 1e-10 bar, the mixed
+    path within its L1 bound (1e-6 of each field's scale)."""
+    n = 64
+    tb = wl.Turbulence(n, seed=111, lorentz_max=5.0)
+    st = (tb.prim5(), tb.bface_background(), tb.apot())
+    L = (2 * np.pi,) * 3
+    g = orc.Grid(n, n, n, *L)
+    g.set_state(*st)
+    assert g.step(5) == 0
+    s = echo.Solver(n, n, n, L=L, precision=precision)
+    s.set_state(*st)
+    done, t = s.step(5)
+    # the mixed path takes the speed maximum (hence dt) in FP32
+    assert done == 5 and t == pytest.approx(g.t, rel=1e-12 if precision == "fp64" else 1e-6)
+    p, ref = s.primitives(), g.primitives()
+    if precision == "fp64":
+        assert_parity(p, ref, PRIM_GROUPS, what="turbulence, Lorentz factor 5, 64^3")
+    else:
+        for grp in PRIM_GROUPS:
+            scale = np.max(np.abs(ref[grp]))
+            for v in grp:
+                assert np.mean(np.abs(p[v] - ref[v])) / scale < 1e-6, v
+    d = s.diagnostics()
+    assert d["c2p_failures"] == 0

@@ -89,3 +89,21 @@ def test_adam_step_hand_computed():
     theta, m, v = mlp.adam_step(theta, [0.05, 0.1, -0.3], m, v, 2, 0.01)
     assert np.allclose(theta, [0.9806782057911869, 2.0126633697281324, 3.0074413678849681],
                        rtol=1e-14, atol=0)
+
+
+def test_f16_rounding_and_inference_model():
+    """The f16 rounding of the inference model is IEEE half, round to nearest even
+    (1 + 2^-11 is a tie that rounds to 1, 1 + 3 * 2^-11 rounds up to 1 + 2^-9, the
+    largest half is 65504), and the rounded forward pass stays within the rounding
+    it models of the exact FP64 network."""
+    assert mlp.f16(1.0 + 2.0 ** -11) == 1.0
+    assert mlp.f16(1.0 + 3 * 2.0 ** -11) == 1.0 + 2.0 ** -9
+    assert mlp.f16(65504.0) == 65504.0 and mlp.f16(-0.1) == np.float16(-0.1)
+    u, B, W = _batch(200, 54)
+    x = mlp.features(u, B)
+    theta = wl.mlp_init(55).astype(np.float64)
+    y, _ = mlp.forward(theta, x)
+    yi, (h1, h2) = mlp.forward_infer(theta, x)
+    assert np.all(np.abs(h1) <= 1.0) and np.all(np.abs(h2) <= 1.0)
+    assert np.array_equal(h1, mlp.f16(h1)) and np.array_equal(h2, mlp.f16(h2))
+    assert 0.0 < np.max(np.abs(yi - y)) < 5e-3
