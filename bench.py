@@ -276,6 +276,8 @@ def main():
     ap.add_argument("--ho", type=int, default=1, help="0: two-point INT and DER")
     ap.add_argument("--rec", default="mp5", choices=["mp5", "linear"])
     ap.add_argument("--rk", type=int, default=3, choices=[2, 3])
+    ap.add_argument("--sweeps", default="auto", choices=["auto", "fused", "separate"],
+                    help="the mixed path's y/z sweep kernels")
     ap.add_argument("--ref-n", type=int, default=64)
     ap.add_argument("--cpu-n", type=int, default=128)   # about 10 s of oracle work
     ap.add_argument("--cpu-steps", type=int, default=6)
@@ -322,7 +324,7 @@ def main():
     L, st = state_for(args, n, device=dev)
     s = echo.Solver(n, n, n, L=L, precision=args.precision, device=local, guess=args.guess,
                     stream=stream.cuda_stream, uct=args.uct, ho=args.ho, rec=args.rec,
-                    rk_order=args.rk)
+                    rk_order=args.rk, sweeps=args.sweeps)
     weights, train_info = None, None
     if args.guess == "mlp":
         weights, train_info = train_guess(args)
@@ -511,7 +513,7 @@ def run_variant(args, n, precision, guess, stream, dev, ref=None, weights=None):
     from paper_2401_03008_gb300 import echo
     L, st = state_for(args, n, device=dev)
     v = echo.Solver(n, n, n, L=L, precision=precision, guess=guess, stream=stream.cuda_stream,
-                    uct=args.uct, ho=args.ho, rec=args.rec, rk_order=args.rk)
+                    uct=args.uct, ho=args.ho, rec=args.rec, rk_order=args.rk, sweeps=args.sweeps)
     if weights is not None:
         v.mlp_load(weights)
     v.set_state(*st)

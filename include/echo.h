@@ -73,6 +73,17 @@ enum { ECHO_FP64 = 0, ECHO_MIXED = 1 };
  * small learned network loaded with echo_mlp_load (falls back to the previous W
  * where its guess is unusable). */
 enum { ECHO_GUESS_PREV = 0, ECHO_GUESS_COLD = 1, ECHO_GUESS_MLP = 2 };
+/* Kernels of the mixed path's y and z sweeps (Sec. 3 steps 2-3).  The fused kernel
+ * stages planes of the primitives in shared memory by TMA and keeps the face fluxes
+ * on chip (REC, fluxes, HLL and DER in one pass); the separate kernels write the
+ * fluxes of one direction and take their DER in a second kernel.  Both compute the
+ * same arithmetic per face, compiled apart, so they agree to FP32 rounding, not bit
+ * for bit.  ECHO_SWEEPS_AUTO: fused where it pays (grids of at least four waves of
+ * blocks); ECHO_SWEEPS_FUSED: fused wherever the grid allows it; ECHO_SWEEPS_SEPARATE:
+ * never.  The fused kernel needs UCT, MP5 and nx a multiple of 4 (rows of 16-byte
+ * multiples for TMA), and at least 8 cells along the direction; elsewhere, and on
+ * the FP64 path, the separate kernels run. */
+enum { ECHO_SWEEPS_AUTO = 0, ECHO_SWEEPS_FUSED = 1, ECHO_SWEEPS_SEPARATE = 2 };
 
 typedef struct {
     int nx, ny, nz;     /* cells per direction, periodic; each >= 1 */
@@ -92,10 +103,12 @@ typedef struct {
     int device;         /* CUDA device ordinal */
     void *stream;       /* cudaStream_t to launch on; NULL: the library makes one */
     int rk_order;       /* 3: SSP-RK3 (default); 2: SSP-RK2 (the faster variant of Sec. 4) */
+    int sweeps;         /* ECHO_SWEEPS_*: the mixed path's y and z sweep kernels */
 } echo_config;
 
 /* Fill *cfg with defaults: 32^3 unit box, gamma 4/3, cfl 0.4, uct 1, ho 1, MP5,
- * FP64, previous-W guess, tol 1e-6, maxit 100, device 0, own stream, SSP-RK3. */
+ * FP64, previous-W guess, tol 1e-6, maxit 100, device 0, own stream, SSP-RK3,
+ * ECHO_SWEEPS_AUTO. */
 echo_status echo_config_default(echo_config *cfg);
 
 /* Validate cfg, select its device, allocate the device state (library-owned) and
@@ -125,7 +138,9 @@ echo_status echo_set_state(echo_ctx *ctx, const double *prim, const double *bfac
  * shortened to land on t_end; pass
  * INFINITY for no limit).  *steps_done and *t_now (either may be NULL) receive
  * the steps taken and the time reached.  On ECHO_ERR_C2P or ECHO_ERR_NONFINITE the
- * state, t and the step count are those at the start of the step that failed.
+ * state, t and the step count are those at the start of the step that failed; so
+ * too on ECHO_ERR_CUDA from a bounded wait of the mixed path's fused sweep that ran
+ * out (a TMA copy that did not arrive).
  * Without t_end (and without kernel timing) the first call captures one full step
  * as a CUDA graph on the context's stream and every step replays it.  The call
  * synchronises its stream before returning, so it cannot itself be captured into a

@@ -15,7 +15,7 @@ namespace {
 const char *kKernelNames[ECHO_NKERNELS] = {
     "int_c2p", "flux_x", "flux_y", "flux_z", "der_x", "der_y", "der_z", "uct_x",
     "uct_y", "uct_z", "rk_curl", "dt", "curl", "init", "diag", "misc", "mlp_guess",
-    "unused17", "unused18", "unused19"};
+    "sweep_y", "sweep_z", "unused19"};
 
 char g_err[256] = "no error";
 
@@ -153,6 +153,7 @@ echo_status echo_config_default(echo_config *cfg)
     cfg->device = 0;
     cfg->stream = nullptr;
     cfg->rk_order = 3;
+    cfg->sweeps = ECHO_SWEEPS_AUTO;
     return ECHO_OK;
 }
 
@@ -172,6 +173,8 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
         return fail(nullptr, ECHO_ERR_ARG, "rec must be ECHO_REC_MP5 or ECHO_REC_LINEAR");
     if (cfg->rk_order != 2 && cfg->rk_order != 3)
         return fail(nullptr, ECHO_ERR_ARG, "rk_order must be 2 or 3");
+    if (cfg->sweeps < ECHO_SWEEPS_AUTO || cfg->sweeps > ECHO_SWEEPS_SEPARATE)
+        return fail(nullptr, ECHO_ERR_ARG, "sweeps must be ECHO_SWEEPS_AUTO, _FUSED or _SEPARATE");
     if (cfg->precision != ECHO_FP64 && cfg->precision != ECHO_MIXED)
         return fail(nullptr, ECHO_ERR_ARG, "precision must be FP64 or MIXED");
     if (cfg->c2p_guess < 0 || cfg->c2p_guess > 2)
@@ -259,6 +262,7 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
             return fail(nullptr, ECHO_ERR_OOM, "device allocation of %zu bytes failed", a.bytes);
         }
     }
+    if (c->mixed) echo::make_sweep_maps(c);
     DevScalars h;
     memset(&h, 0, sizeof(h));
     h.cfl = cfg->cfl;
@@ -435,18 +439,25 @@ echo_status run_steps(echo_ctx *c, int max_steps, double t_end, int *steps_done,
     if ((st = sync_check(c))) return st;
     if ((st = read_sc(c, &h))) return st;
     echo_status ret = ECHO_OK;
-    if (h.halt & 1) {
-        // roll back to the start of the failed step
+    if (h.halt & 5) {
+        // roll back to the start of the failed step (bit 0: an inversion failed;
+        // bit 2: a bounded wait of the fused sweep ran out)
         if (h.fail_stage >= 2) {
             echo::launch_copy_state(c, c->U, c->Bf, c->U0, c->Bf0);
             echo::launch_bf32(c);
             h.t = h.t_prev;
         }
+        const int why = h.halt;
         h.halt = 0;
         if ((st = write_sc(c, &h))) return st;
         if ((st = sync_check(c))) return st;
-        ret = fail(c, ECHO_ERR_C2P, "inversion failed in step %ld (stage %d, %u cells)",
-                   h.fail_step, h.fail_stage, h.fails);
+        if (why & 1)
+            ret = fail(c, ECHO_ERR_C2P, "inversion failed in step %ld (stage %d, %u cells)",
+                       h.fail_step, h.fail_stage, h.fails);
+        else
+            ret = fail(c, ECHO_ERR_CUDA,
+                       "a bounded wait for a TMA copy of the fused sweep ran out in step %ld; "
+                       "the step was rolled back", h.fail_step);
     }
     if (steps_done) *steps_done = (int)(h.step - step0);
     if (t_now) *t_now = h.t;
@@ -540,12 +551,14 @@ echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *am
     if ((st = sync_check(c))) return st;
     if ((st = read_sc(c, &h))) return st;
     if (amax) memcpy(amax, &h.amax_bits, sizeof(double));
-    bool bad = h.halt & 1;
+    const int why = h.halt;
     h.halt = 0;
     h.amax_bits = 0;
     h.fail_stage = 0;
     if ((st = write_sc(c, &h))) return st;
-    if (bad) return fail(c, ECHO_ERR_C2P, "inversion failed in %u cells", h.fails);
+    if (why & 1) return fail(c, ECHO_ERR_C2P, "inversion failed in %u cells", h.fails);
+    if (why & 4)
+        return fail(c, ECHO_ERR_CUDA, "a bounded wait for a TMA copy of the fused sweep ran out");
     if (ptr_kind != ECHO_PTR_DEVICE) {
         if (rhs_cons && (st = output(c, rhs_cons, dc, 5 * n, ptr_kind))) return st;
         if (rhs_face && (st = output(c, rhs_face, df, 3 * n, ptr_kind))) return st;

@@ -444,7 +444,8 @@ echo_status echo_decomp_step(echo_decomp *d, int max_steps, double t_end, int *s
     if ((st = sync_d(d))) return st;
     if ((st = read_sc(d, &h))) return st;
     echo_status ret = ECHO_OK;
-    if (h.halt & 1) {
+    if (h.halt & 5) {
+        // bit 0: an inversion failed; bit 2: a bounded wait of the fused sweep ran out
         if (h.fail_stage >= 2) {
             for (echo_ctx *c : d->sub) {
                 echo::launch_copy_state(c, c->U, c->Bf, c->U0, c->Bf0);
@@ -452,11 +453,17 @@ echo_status echo_decomp_step(echo_decomp *d, int max_steps, double t_end, int *s
             }
             h.t = h.t_prev;
         }
+        const int why = h.halt;
         h.halt = 0;
         if ((st = write_sc(d, &h))) return st;
         if ((st = sync_d(d))) return st;
-        ret = dfail(d, ECHO_ERR_C2P, "inversion failed in step %ld (stage %d, %u cells)",
-                    h.fail_step, h.fail_stage, h.fails);
+        if (why & 1)
+            ret = dfail(d, ECHO_ERR_C2P, "inversion failed in step %ld (stage %d, %u cells)",
+                        h.fail_step, h.fail_stage, h.fails);
+        else
+            ret = dfail(d, ECHO_ERR_CUDA,
+                        "a bounded wait for a TMA copy of the fused sweep ran out in step %ld; "
+                        "the step was rolled back", h.fail_step);
     }
     if (steps_done) *steps_done = (int)(h.step - step0);
     if (t_now) *t_now = h.t;

@@ -69,7 +69,8 @@ struct DevScalars {
     unsigned int fails;            // failed inversions
     unsigned int fallbacks;        // rejected learned guesses
     unsigned int rec_fallbacks;    // interface states reset to first order
-    int halt;                      // bit 0: inversion failed, bit 1: t_end reached
+    int halt;                      // bit 0: inversion failed, bit 1: t_end reached, bit 2: a
+                                   // bounded wait of the fused sweep ran out
     int fail_stage;                // stage (1..3) of the first failure, 0 if none
     long fail_step;                // step index of the first failure
     long step;                     // steps completed

@@ -1,6 +1,7 @@
 // Host-side context of libecho (shared by the API and the kernel translation units).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -14,7 +15,8 @@ namespace echo {
 // kernel kinds for launch counting and event timing
 enum Kind {
     K_C2P = 0, K_FLUX_X, K_FLUX_Y, K_FLUX_Z, K_DER_X, K_DER_Y, K_DER_Z,
-    K_UCT_X, K_UCT_Y, K_UCT_Z, K_RK, K_DT, K_CURL, K_INIT, K_DIAG, K_MISC, K_MLP
+    K_UCT_X, K_UCT_Y, K_UCT_Z, K_RK, K_DT, K_CURL, K_INIT, K_DIAG, K_MISC, K_MLP,
+    K_SWEEP_Y, K_SWEEP_Z
 };
 
 struct ProfRec {
@@ -59,6 +61,11 @@ struct echo_ctx {
     long graph_kernels;     // kernels in one replay (for the launch count)
     bool graph_failed;      // capture not possible on this stream: launch directly
     unsigned mlp_blocks;    // persistent grid of the learned-guess kernel (0: not loaded)
+    // mixed path: TMA descriptors of the float primitive array for the fused y and z
+    // sweeps (index 1, 2) and their segment lengths (0: that direction takes the
+    // separate flux and DER kernels)
+    CUtensorMap tm_prim[3];
+    int sweep_T[3];
     std::vector<echo::ProfRec> prof;
     long prof_count[ECHO_NKERNELS];
     double prof_ms[ECHO_NKERNELS];
@@ -145,6 +152,11 @@ double probe_fma_peak(echo_ctx *c, int fp64);
 void set_global_error(const char *msg);
 // drop the captured step graph (the launch set changed)
 void drop_step_graph(echo_ctx *c);
+// mixed path: choose the y/z sweep kernels (cfg.sweeps and the grid) and build the
+// TMA descriptors of the fused ones (c->sweep_T)
+void make_sweep_maps(echo_ctx *c);
+// mixed path: the fused reconstruction + flux + DER sweep along D = 1, 2
+void launch_fused_sweep(echo_ctx *c, int D, int want_amax);
 // harvest of training states (features, converged W/U) of cells offset + q stride
 // into slots base + q (those below capacity); returns the number of such cells
 long launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,

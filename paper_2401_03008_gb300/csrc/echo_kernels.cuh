@@ -591,12 +591,22 @@ void Path<R>::sweeps(echo_ctx *c, int want_amax)
     launch(c, K_FLUX_X, k_flux<R, 0>, nb0, BS, 0, g, prim, bf, flux,
            (R *)c->fdat[0], c->sc, want_amax);
     launch(c, K_DER_X, k_der<R, 0>, nd0, BS, 0, g, (const R *)flux, rhs, 1, c->sc);
-    launch(c, K_FLUX_Y, k_flux<R, 1>, nb1, BS, 0, g, prim, bf, flux,
-           (R *)c->fdat[1], c->sc, want_amax);
-    launch(c, K_DER_Y, k_der<R, 1>, nd1, BS, 0, g, (const R *)flux, rhs, 0, c->sc);
-    launch(c, K_FLUX_Z, k_flux<R, 2>, nb2, BS, 0, g, prim, bf, flux,
-           (R *)c->fdat[2], c->sc, want_amax);
-    launch(c, K_DER_Z, k_der<R, 2>, nd2, BS, 0, g, (const R *)flux, rhs, 0, c->sc);
+    // mixed path: y and z as fused sweeps where chosen (TMA-staged planes, the face
+    // fluxes kept on chip), else the flux kernel and its DER
+    if (sizeof(R) == 4 && c->sweep_T[1]) {
+        launch_fused_sweep(c, 1, want_amax);
+    } else {
+        launch(c, K_FLUX_Y, k_flux<R, 1>, nb1, BS, 0, g, prim, bf, flux,
+               (R *)c->fdat[1], c->sc, want_amax);
+        launch(c, K_DER_Y, k_der<R, 1>, nd1, BS, 0, g, (const R *)flux, rhs, 0, c->sc);
+    }
+    if (sizeof(R) == 4 && c->sweep_T[2]) {
+        launch_fused_sweep(c, 2, want_amax);
+    } else {
+        launch(c, K_FLUX_Z, k_flux<R, 2>, nb2, BS, 0, g, prim, bf, flux,
+               (R *)c->fdat[2], c->sc, want_amax);
+        launch(c, K_DER_Z, k_der<R, 2>, nd2, BS, 0, g, (const R *)flux, rhs, 0, c->sc);
+    }
 }
 
 template <typename R>

@@ -50,7 +50,8 @@ class Config(C.Structure):
                 ("uct", C.c_int), ("ho", C.c_int), ("rec", C.c_int),
                 ("precision", C.c_int), ("c2p_guess", C.c_int),
                 ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
-                ("device", C.c_int), ("stream", C.c_void_p), ("rk_order", C.c_int)]
+                ("device", C.c_int), ("stream", C.c_void_p), ("rk_order", C.c_int),
+                ("sweeps", C.c_int)]
 
 
 class TrainCfg(C.Structure):
@@ -155,7 +156,7 @@ def _ptr(x, what, count):
 
 def make_config(nx, ny, nz, L=(1.0, 1.0, 1.0), gamma=4.0 / 3.0, cfl=0.4, ho=1,
                 precision="fp64", guess="prev", tol=1e-6, maxit=100, device=0, stream=None,
-                uct=1, rec="mp5", rk_order=3):
+                uct=1, rec="mp5", rk_order=3, sweeps="auto"):
     """echo_config from keyword arguments (the defaults of echo_config_default)."""
     cfg = Config()
     lib().echo_config_default(C.byref(cfg))
@@ -173,6 +174,7 @@ def make_config(nx, ny, nz, L=(1.0, 1.0, 1.0), gamma=4.0 / 3.0, cfl=0.4, ho=1,
     cfg.c2p_maxit = maxit
     cfg.device = device
     cfg.stream = stream
+    cfg.sweeps = {"auto": 0, "fused": 1, "separate": 2}[sweeps]
     return cfg
 
 

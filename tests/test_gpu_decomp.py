@@ -43,19 +43,38 @@ def _same(s, d):
     return all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])) and a[3:] == b[3:]
 
 
-@pytest.mark.parametrize("kw", [dict(), dict(ho=0), dict(uct=0), dict(uct=0, ho=0),
-                                dict(rec="linear", rk_order=2), dict(precision="mixed"),
-                                dict(guess="cold")],
+# The mixed path's y and z sweeps can run as one fused kernel, which needs a grid
+# whose x extent is a multiple of 4 (TMA rows), or as separate flux and DER kernels:
+# the same arithmetic per face, compiled apart, so the two agree to FP32 rounding
+# only.  With the fused kernel forced, the y/z split keeps the padded blocks
+# (24 x 24 x 22) on it like the grid (24 x 20 x 16).
+@pytest.mark.parametrize("kw,blocks", [(dict(), (2, 2, 2)), (dict(ho=0), (2, 2, 2)),
+                                       (dict(uct=0), (2, 2, 2)), (dict(uct=0, ho=0), (2, 2, 2)),
+                                       (dict(rec="linear", rk_order=2), (2, 2, 2)),
+                                       (dict(precision="mixed"), (2, 2, 2)),
+                                       (dict(precision="mixed", sweeps="fused"), (1, 2, 2)),
+                                       (dict(guess="cold"), (2, 2, 2))],
                          ids=["uct-ho-mp5", "ho0", "uct0", "uct0-ho0", "linear-rk2", "mixed",
-                              "cold"])
-def test_blocks_bit_identical_at_min_halo(kw):
-    s, d, r1, r2 = _pair((2, 2, 2), **kw)
+                              "mixed-fused", "cold"])
+def test_blocks_bit_identical_at_min_halo(kw, blocks):
+    s, d, r1, r2 = _pair(blocks, **kw)
     assert r1 == r2 and r1[0] == 3
     assert _same(s, d)
     assert np.array_equal(s.primitives(), d.primitives())
     ds, dc = s.diagnostics(), d.counters()
     assert dc["c2p_calls"] == ds["c2p_calls"] and dc["newton_it_max"] == ds["newton_it_max"]
     assert dc["newton_it_sum"] == pytest.approx(ds["newton_it_mean"] * ds["c2p_calls"], rel=1e-12)
+
+
+def test_mixed_blocks_with_the_separate_sweeps():
+    """Mixed path with the fused sweep forced, blocks split along x too: the padded
+    blocks (26 cells along x) cannot take it and run the separate flux and DER
+    kernels while the grid runs the fused sweep; the owned cells agree to FP32
+    rounding (the field scale's 1e-6)."""
+    s, d, r1, r2 = _pair((2, 2, 2), precision="mixed", sweeps="fused")
+    assert r1[0] == r2[0] == 3 and r1[1] == pytest.approx(r2[1], rel=1e-6)
+    assert_parity(d.primitives(), s.primitives(), PRIM_GROUPS, tol=1e-6,
+                  what="mixed blocks vs grid")
 
 
 @pytest.mark.parametrize("blocks", [(3, 1, 1), (1, 2, 1), (1, 1, 4), (2, 5, 1), (4, 2, 2)])

@@ -427,3 +427,60 @@ def test_diagnostics_match_oracle(ho):
     bad[2, 5, 6, 7] = np.nan
     s.set_conserved(bad, bfr, w, t, step)
     assert s.diagnostics()["nonfinite"] == 1
+
+
+@pytest.mark.parametrize("sweeps", ["fused", "separate"])
+def test_mixed_sweep_kernels_against_oracle(sweeps):
+    """The mixed path with each kind of y/z sweep kernel (the fused TMA sweep forced
+    on a grid small enough that the automatic choice would not take it): one
+    right-hand side of a smooth state on 40 x 24 x 20 and 20 steps of the 32^3 wave,
+    against the FP64 oracle within the FP32 rounding of the reconstruction."""
+    n, L = (40, 24, 20), (1.0, 0.8, 0.6)
+    g, s = make_pair(n, L=L, precision="mixed", sweeps=sweeps, state=smooth(n, 39, L=L))
+    cons0 = g.cons.copy()
+    rc, rb, amax, bad = g.rhs()
+    grc, grb, gamax = s.rhs()
+    assert gamax == pytest.approx(amax, rel=1e-6)
+    hmin = min(L[d] / n[d] for d in range(3))
+    for got, ref, q, groups in ((grc, rc, cons0, CONS_GROUPS), (grb, rb, g.bf, FACE_GROUPS)):
+        for grp in groups:
+            floor = np.max(np.abs(q[grp])) * amax / hmin
+            assert_parity(got[grp], ref[grp], [list(range(len(grp)))], tol=2e-6, floor=floor,
+                          what="mixed rhs (%s sweeps)" % sweeps)
+    c, st = cpa_state((32, 32, 32), (1, 0, 0))
+    g, s = make_pair((32, 32, 32), precision="mixed", sweeps=sweeps, state=st)
+    g.step(20)
+    s.step(20)
+    p, ref = s.primitives(), g.primitives()
+    for grp in PRIM_GROUPS:
+        scale = np.max(np.abs(ref[grp]))
+        for v in grp:
+            assert np.mean(np.abs(p[v] - ref[v])) / scale < 1e-6, (sweeps, v)
+
+
+def test_fused_sweep_agrees_with_separate_and_repeats_bit_for_bit():
+    """The turbulence at its full amplitude on 96^3, where most warps limit some
+    reconstructions: the fused sweep gives the separate kernels' right-hand side to
+    FP32 rounding, and exactly the same bits on every repetition (each thread waits
+    for every plane it reads, including the first ones of its segment)."""
+    n = 96
+    tb = wl.Turbulence(n, seed=2401_03008, lorentz_max=5.0)
+    st = (tb.prim5(), tb.bface_background(), tb.apot())
+    L = (2 * np.pi,) * 3
+    out = {}
+    for sweeps in ("fused", "separate"):
+        s = echo.Solver(n, n, n, L=L, precision="mixed", sweeps=sweeps)
+        reps = []
+        for rep in range(3):
+            s.set_state(*st)
+            reps.append(s.rhs())
+        s.close()
+        for r in reps[1:]:
+            assert np.array_equal(r[0], reps[0][0]) and np.array_equal(r[1], reps[0][1])
+            assert r[2] == reps[0][2]
+        out[sweeps] = reps[0]
+    (fc, fb, fa), (sc_, sb, sa) = out["fused"], out["separate"]
+    assert fa == pytest.approx(sa, rel=1e-6)
+    scale = np.abs(sc_).max(axis=(1, 2, 3)).max()
+    assert np.max(np.abs(fc - sc_)) <= 1e-4 * scale
+    assert np.max(np.abs(fb - sb)) <= 1e-4 * np.abs(sb).max()
