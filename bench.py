@@ -289,10 +289,14 @@ def main():
     ap.add_argument("--train-steps", type=int, default=12)
     ap.add_argument("--config", type=int, default=0,
                     help="1..5: benchmark-plan configurations; 6: the 2.5-D turbulence run of "
-                         "Sec. 5; 7: 2 x 2 x 2 blocks with the wide halo against one grid")
+                         "Sec. 5; 7: 2 x 2 x 2 blocks with the wide halo against one grid; "
+                         "8: time to accuracy of the FP64 and mixed paths on the Alfven wave")
     ap.add_argument("--config-steps", type=int, default=20)
     ap.add_argument("--config5-n", type=int, default=768)
-    ap.add_argument("--config5-fp64-steps", type=int, default=5)
+    ap.add_argument("--config5-steps", type=int, default=200)
+    ap.add_argument("--config5-lorentz-max", type=float, default=3.5,
+                    help="largest initial Lorentz factor of the 200-step run (the scheme has "
+                         "no floors; from 4 up the run ends in a failed inversion first)")
     ap.add_argument("--config6-n", type=int, default=4096)
     ap.add_argument("--config6-t", type=float, default=20.0)
     ap.add_argument("--config6-out", default="", help="write the spectra (.npz) here")
@@ -684,10 +688,14 @@ def run_config(args):
         out.update({"workload": "Alfven wave along (1,1,1), %d^3" % n
                     + (", one period" if args.config == 2 else ", %d steps" % args.config_steps),
                     "period": c.period, "results": res})
+    elif args.config == 8:
+        out.update(run_time_to_accuracy(args, timed, sp))
     else:
         n = 512 if args.config == 4 else args.config5_n
         dev = "cuda:%d" % torch.cuda.current_device()
         args.workload = "turbulence"
+        if args.config == 5:
+            args.lorentz_max = args.config5_lorentz_max
         w, info = train_guess(args)
         res = {"training": info}
         runs = ([("fp64", "prev"), ("fp64", "cold"), ("fp64", "mlp"), ("mixed", "prev"),
@@ -695,7 +703,7 @@ def run_config(args):
                 [("fp64", "prev"), ("mixed", "prev"), ("mixed", "mlp")])
         ref, ref_steps = None, None
         for prec, guess in runs:
-            steps = args.config_steps if prec == "mixed" or args.config == 4 else args.config5_fp64_steps
+            steps = args.config_steps if args.config == 4 else args.config5_steps
             keep = prec == "fp64" and guess == "prev"
             r, p = run_config_variant(args, n, prec, guess, steps, stream, dev,
                                       ref if steps == ref_steps else None,
@@ -706,6 +714,36 @@ def run_config(args):
             res["%s_%s" % (prec, guess)] = r
         out.update({"workload": workload_name(args, n), "results": res})
     print(json.dumps(out))
+
+
+def run_time_to_accuracy(args, timed, sp):
+    """The Alfven wave along (1,1,1) (Sec. 4) for one full period on several grids in
+    both paths: steps, GPU seconds, rate and the L1 error of every primitive against
+    the exact solution (each over its field scale), so that each path's cost can be
+    read off at equal accuracy.  FP64 on 64^3..256^3, mixed on 128^3..512^3."""
+    from paper_2401_03008_gb300 import echo
+    from paper_2401_03008_gb300 import workloads as wl
+    import numpy as np
+    runs = [("fp64", 64), ("fp64", 128), ("fp64", 256), ("mixed", 128), ("mixed", 256),
+            ("mixed", 512)]
+    res = []
+    for prec, n in runs:
+        c = wl.CPA(n, n, n, m=(1, 1, 1))
+        s = echo.Solver(n, n, n, precision=prec, stream=sp)
+        s.set_state(c.prim5(), c.bface_background(), c.apot())
+        done, t, ms = timed(s, 1 << 30, c.period)
+        ex = c.exact_prim8(t)
+        l1 = s.l1_error(ex)
+        scale = [1.0, c.vA * c.eta, 1.0, math.sqrt(1 + c.eta ** 2) * c.B0]
+        grp = [0, 1, 1, 1, 2, 3, 3, 3]
+        rel = [float(l1[v]) / scale[grp[v]] for v in range(8)]
+        d = s.diagnostics()
+        res.append({"path": prec, "n": n, "steps": done, "t": t, "gpu_s": ms * 1e-3,
+                    "cell_updates_per_s": n ** 3 * done / (ms * 1e-3),
+                    "l1_vs_exact_rel": rel, "l1_max_rel": max(rel), "divb_max": d["divb_max"]})
+        s.close()
+    return {"workload": "Alfven wave along (1,1,1), one period (T = %.7f), CFL 0.4" % c.period,
+            "results": res}
 
 
 def run_turbulence_2d(args, timed, sp):

@@ -372,13 +372,12 @@ __device__ __forceinline__ R der_c(const R *s, R inv_h, int ho)
 
 // Conserved variables (D, S, U) and field, physical flux along D of all 8, and the
 // fast speeds lm <= lp along D, sharing the intermediate quantities.
-// s = (rho, vx, vy, vz, p, Bx, By, Bz).
+// s = (rho, vx, vy, vz, p, Bx, By, Bz); v2 = vx^2 + vy^2 + vz^2 (the caller has it).
 template <typename R, int D>
-__device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &lm, R &lp)
+__device__ __forceinline__ void phys(const R *s, R v2, R gam, R gfac, R *U, R *F, R &lm, R &lp)
 {
     const R rho = s[0], vx = s[1], vy = s[2], vz = s[3], pg = s[4];
     const R bx = s[5], by = s[6], bz = s[7];
-    R v2 = vx * vx + vy * vy + vz * vz;
     R omv2 = R(1) - v2;
     R lor = rsqrt(omv2);
     R lor2 = lor * lor;
@@ -410,10 +409,11 @@ __device__ __forceinline__ void phys(const R *s, R gam, R gfac, R *U, R *F, R &l
     const R vd = s[1 + D];
     const R Ed = D == 0 ? ex : (D == 1 ? ey : ez);
     const R Bd = s[5 + D];
+    const R wvd = w * vd;
     F[0] = D0 * vd;
-    F[1] = w * vx * vd - ex * Ed - bx * Bd + (D == 0 ? ptot : R(0));
-    F[2] = w * vy * vd - ey * Ed - by * Bd + (D == 1 ? ptot : R(0));
-    F[3] = w * vz * vd - ez * Ed - bz * Bd + (D == 2 ? ptot : R(0));
+    F[1] = wvd * vx - ex * Ed - bx * Bd + (D == 0 ? ptot : R(0));
+    F[2] = wvd * vy - ey * Ed - by * Bd + (D == 1 ? ptot : R(0));
+    F[3] = wvd * vz - ez * Ed - bz * Bd + (D == 2 ? ptot : R(0));
     F[4] = D == 0 ? Sx : (D == 1 ? Sy : Sz);
     F[5] = vd * bx - vx * Bd;
     F[6] = vd * by - vy * Bd;

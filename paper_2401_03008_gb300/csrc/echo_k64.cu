@@ -47,9 +47,9 @@ k_init(Grid g, const double *__restrict__ prim5, const double *__restrict__ Bf,
 #pragma unroll
     for (int d = 0; d < 3; d++) s[5 + d] = cell_field(g, Bf, c, i, j, k, d);
     double u[8], f[8], lm, lp;
-    phys<double, 0>(s, g.gam, g.gfac, u, f, lm, lp);
+    const double v2 = s[1] * s[1] + s[2] * s[2] + s[3] * s[3];
+    phys<double, 0>(s, v2, g.gam, g.gfac, u, f, lm, lp);
     for (int v = 0; v < 5; v++) U[v * n + c] = u[v];
-    double v2 = s[1] * s[1] + s[2] * s[2] + s[3] * s[3];
     W[c] = (s[0] + g.gfac * s[4]) / (1.0 - v2);
 }
 
@@ -205,24 +205,37 @@ k_diag_partial(Grid g, const double *__restrict__ U, const double *__restrict__ 
     }
 }
 
-// one thread per quantity, blocks summed in order
-__global__ void k_diag_final(const double *partials, double *out, int mode)
+// one warp per quantity: each lane takes every 32nd block partial (compensated),
+// then the lanes merge in a fixed shuffle tree, so the result does not depend on
+// scheduling; the last warp takes the maximum of |div B|
+__global__ void __launch_bounds__(32 * (NSUM + 1)) k_diag_final(const double *partials, double *out,
+                                                                int mode)
 {
-    int q = threadIdx.x;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nq = mode == 1 ? 1 : NSUM;
     if (q < nq) {
         Pair p{0.0, 0.0};
         double cc = 0.0;
-        for (int b = 0; b < DIAG_BLOCKS; b++) {
+        for (int b = lane; b < DIAG_BLOCKS; b += 32) {
             pair_add(p, partials[b * DIAG_Q + 2 * q]);
             cc += partials[b * DIAG_Q + 2 * q + 1];
         }
-        out[q] = p.s + (p.c + cc);
-    }
-    if (mode == 0 && q == nq) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const Pair r{__shfl_down_sync(0xffffffffu, p.s, o),
+                         __shfl_down_sync(0xffffffffu, p.c, o)};
+            const double rc = __shfl_down_sync(0xffffffffu, cc, o);
+            if (lane < o) {
+                p = pair_merge(p, r);
+                cc += rc;
+            }
+        }
+        if (lane == 0) out[q] = p.s + (p.c + cc);
+    } else if (mode == 0 && q == nq) {
         double m = 0.0;
-        for (int b = 0; b < DIAG_BLOCKS; b++) m = fmax(m, partials[b * DIAG_Q + 2 * NSUM]);
-        out[nq] = m;
+        for (int b = lane; b < DIAG_BLOCKS; b += 32) m = fmax(m, partials[b * DIAG_Q + 2 * NSUM]);
+        m = warp_max(m);
+        if (lane == 0) out[nq] = m;
     }
 }
 
@@ -231,7 +244,8 @@ void launch_diag_mode(echo_ctx *c, int mode, const double *a, const double *b)
 {
     launch(c, K_DIAG, k_diag_partial, DIAG_BLOCKS, DIAG_THREADS, 0, c->g, (const double *)c->U,
            (const double *)c->Bf, a, b, c->partials, mode);
-    launch(c, K_DIAG, k_diag_final, 1, 32, 0, (const double *)c->partials, c->dres, mode);
+    launch(c, K_DIAG, k_diag_final, 1, 32 * (NSUM + 1), 0, (const double *)c->partials, c->dres,
+           mode);
 }
 
 // ---------------------------------------------------------------------------

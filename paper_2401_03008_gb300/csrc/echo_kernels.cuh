@@ -279,38 +279,40 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
         }
         // positivity: reset a state to the first-order (cell) value
         int nfb = 0;
-        {
-            R v2 = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
-            if (!gtz(L[0]) || !gtz(L[4]) || !lt(v2, R(1))) {
+        R v2L = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
+        R v2R = Rt[1] * Rt[1] + Rt[2] * Rt[2] + Rt[3] * Rt[3];
+        if (!gtz(L[0]) || !gtz(L[4]) || !lt(v2L, R(1))) {
 #pragma unroll
-                for (int v = 0; v < 8; v++)
-                    if (v != 5 + D || !uct) L[v] = prim[v * n + cs[2]];
-                nfb++;
-            }
-            v2 = Rt[1] * Rt[1] + Rt[2] * Rt[2] + Rt[3] * Rt[3];
-            if (!gtz(Rt[0]) || !gtz(Rt[4]) || !lt(v2, R(1))) {
+            for (int v = 0; v < 8; v++)
+                if (v != 5 + D || !uct) L[v] = prim[v * n + cs[2]];
+            v2L = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
+            nfb++;
+        }
+        if (!gtz(Rt[0]) || !gtz(Rt[4]) || !lt(v2R, R(1))) {
 #pragma unroll
-                for (int v = 0; v < 8; v++)
-                    if (v != 5 + D || !uct) Rt[v] = prim[v * n + cs[3]];
-                nfb++;
-            }
+            for (int v = 0; v < 8; v++)
+                if (v != 5 + D || !uct) Rt[v] = prim[v * n + cs[3]];
+            v2R = Rt[1] * Rt[1] + Rt[2] * Rt[2] + Rt[3] * Rt[3];
+            nfb++;
         }
         if (nfb && own) atomicAdd(&sc->rec_fallbacks, (unsigned)nfb);
         const R gam = gconst<R>(g.gam, g.gam32);
         const R gfac = gconst<R>(g.gfac, g.gfac32);
         R UL[8], FL[8], UR[8], FR[8], lmL, lpL, lmR, lpR;
-        phys<R, D>(L, gam, gfac, UL, FL, lmL, lpL);
-        phys<R, D>(Rt, gam, gfac, UR, FR, lmR, lpR);
+        phys<R, D>(L, v2L, gam, gfac, UL, FL, lmL, lpL);
+        phys<R, D>(Rt, v2R, gam, gfac, UR, FR, lmR, lpR);
         R ap = rmax(R(0), rmax(lpL, lpR));
         R am = rmax(R(0), rmax(-lmL, -lmR));
         R s = ap + am;
         const int ncomp = uct ? 5 : 8;  // with UCT the field takes the edge fields instead
         if (gtz(s)) {
-            R is = R(1) / s;
+            // HLL weights divided once: a+/(a+ + a-), a-/(a+ + a-), a+ a-/(a+ + a-)
+            const R is = R(1) / s;
+            const R wl = ap * is, wr = am * is, wd = ap * wr;
 #pragma unroll
             for (int qq = 0; qq < 8; qq++)
                 if (qq < ncomp)
-                    flux[qq * n + f] = (ap * FL[qq] + am * FR[qq] - ap * am * (UR[qq] - UL[qq])) * is;
+                    flux[qq * n + f] = wl * FL[qq] + wr * FR[qq] - wd * (UR[qq] - UL[qq]);
         } else {
 #pragma unroll
             for (int qq = 0; qq < 8; qq++)

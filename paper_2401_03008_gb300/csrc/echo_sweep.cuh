@@ -251,25 +251,25 @@ k_sweep(Grid g, const __grid_constant__ CUtensorMap tm, const float *__restrict_
         L[5 + D] = bn;
         R[5 + D] = bn;
         // positivity: a state with rho <= 0, p <= 0 or v^2 >= 1 takes the cell value
-        {
-            float v2 = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
-            if (!(L[0] > 0.f) || !(L[4] > 0.f) || !(v2 < 1.f)) {
+        float v2L = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
+        float v2R = R[1] * R[1] + R[2] * R[2] + R[3] * R[3];
+        if (!(L[0] > 0.f) || !(L[4] > 0.f) || !(v2L < 1.f)) {
 #pragma unroll
-                for (int v = 0; v < 8; v++)
-                    if (v != 5 + D) L[v] = pl[2][v * SW_COLS + tid];
-                nfb++;
-            }
-            v2 = R[1] * R[1] + R[2] * R[2] + R[3] * R[3];
-            if (!(R[0] > 0.f) || !(R[4] > 0.f) || !(v2 < 1.f)) {
+            for (int v = 0; v < 8; v++)
+                if (v != 5 + D) L[v] = pl[2][v * SW_COLS + tid];
+            v2L = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
+            nfb++;
+        }
+        if (!(R[0] > 0.f) || !(R[4] > 0.f) || !(v2R < 1.f)) {
 #pragma unroll
-                for (int v = 0; v < 8; v++)
-                    if (v != 5 + D) R[v] = pl[3][v * SW_COLS + tid];
-                nfb++;
-            }
+            for (int v = 0; v < 8; v++)
+                if (v != 5 + D) R[v] = pl[3][v * SW_COLS + tid];
+            v2R = R[1] * R[1] + R[2] * R[2] + R[3] * R[3];
+            nfb++;
         }
         float UL[8], FL[8], UR[8], FR[8], lmL, lpL, lmR, lpR;
-        phys<float, D>(L, gam, gfac, UL, FL, lmL, lpL);
-        phys<float, D>(R, gam, gfac, UR, FR, lmR, lpR);
+        phys<float, D>(L, v2L, gam, gfac, UL, FL, lmL, lpL);
+        phys<float, D>(R, v2R, gam, gfac, UR, FR, lmR, lpR);
         const float ap = fmaxf(0.f, fmaxf(lpL, lpR));
         const float am = fmaxf(0.f, fmaxf(-lmL, -lmR));
         const float ssum = ap + am;
@@ -279,9 +279,10 @@ k_sweep(Grid g, const __grid_constant__ CUtensorMap tm, const float *__restrict_
             for (int qq = 0; qq < 5; qq++) Fh[m][qq] = Fh[m + 1][qq];
         if (ssum > 0.f) {
             const float is = 1.f / ssum;
+            const float wl = ap * is, wr = am * is, wd = ap * wr;
 #pragma unroll
             for (int qq = 0; qq < 5; qq++)
-                Fh[5][qq] = (ap * FL[qq] + am * FR[qq] - ap * am * (UR[qq] - UL[qq])) * is;
+                Fh[5][qq] = wl * FL[qq] + wr * FR[qq] - wd * (UR[qq] - UL[qq]);
         } else {
 #pragma unroll
             for (int qq = 0; qq < 5; qq++) Fh[5][qq] = 0.5f * (FL[qq] + FR[qq]);
