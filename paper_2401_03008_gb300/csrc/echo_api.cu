@@ -198,21 +198,19 @@ echo_status echo_create(const echo_config *cfg, echo_ctx **out)
     g.ny = cfg->ny;
     g.nz = cfg->nz;
     g.n = n;
-    g.h[0] = cfg->lx / cfg->nx;
-    g.h[1] = cfg->ly / cfg->ny;
-    g.h[2] = cfg->lz / cfg->nz;
-    for (int d = 0; d < 3; d++) g.inv_h[d] = 1.0 / g.h[d];
-    g.hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
     g.gam = cfg->gamma_ad;
     g.gfac = cfg->gamma_ad / (cfg->gamma_ad - 1.0);
     g.gm1g = (cfg->gamma_ad - 1.0) / cfg->gamma_ad;
     g.gm1g32 = (float)g.gm1g;
     g.gam32 = (float)g.gam;
     g.gfac32 = (float)g.gfac;
-    for (int d = 0; d < 3; d++) g.inv_h32[d] = (float)g.inv_h[d];
     g.ho = cfg->ho;
     g.uct = cfg->uct;
     g.rec = cfg->rec;
+    {
+        const double h[3] = {cfg->lx / cfg->nx, cfg->ly / cfg->ny, cfg->lz / cfg->nz};
+        echo::set_spacing(g, h);
+    }
     g.lo[0] = g.lo[1] = g.lo[2] = 0;
     g.hi[0] = g.nx;
     g.hi[1] = g.ny;

@@ -325,14 +325,11 @@ echo_status echo_decomp_create(const echo_config *cfg, int px, int py, int pz, i
             return st;
         }
         d->sub.push_back(c);
+        echo::set_spacing(c->g, h);
         for (int a = 0; a < 3; a++) {
-            c->g.h[a] = h[a];
-            c->g.inv_h[a] = 1.0 / h[a];
-            c->g.inv_h32[a] = (float)c->g.inv_h[a];
             c->g.lo[a] = gm.G[a];
             c->g.hi[a] = gm.G[a] + gm.nloc[a];
         }
-        c->g.hmin = fmin(h[0], fmin(h[1], h[2]));
         c->g.primary = s == 0;
         cudaFree(c->sc);
         c->sc = nullptr;

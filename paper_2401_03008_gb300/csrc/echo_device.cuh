@@ -26,6 +26,10 @@ struct Grid {
     // FP32 copies of the constants the mixed path's FP32 kernels use (a conversion
     // in the kernel would issue on the FP64 pipe)
     float gm1g32, gam32, gfac32, inv_h32[3];
+    // DER weights per direction, divided by h: (75/64, 25/384, 3/640)/h with HO,
+    // (1/h, 0, 0) without (set_spacing)
+    double derw[3][3];
+    float derw32[3][3];
     int ho;            // high-order INT / DER
     int uct;           // 1: staggered field + UCT; 0: cell-centred field, 8-component HLL
     int rec;           // 0: MP5; 1: linear with the MC limiter
@@ -36,10 +40,39 @@ struct Grid {
     int primary;       // 1: this grid advances the step counter
 };
 
+// Cell sizes and what derives from them (1/h, the DER weights in both precisions,
+// the smallest h); ho must be set first.
+inline void set_spacing(Grid &g, const double h[3])
+{
+    for (int d = 0; d < 3; d++) {
+        g.h[d] = h[d];
+        g.inv_h[d] = 1.0 / h[d];
+        g.inv_h32[d] = (float)g.inv_h[d];
+        const double w[3] = {g.ho ? 75.0 / 64.0 : 1.0, g.ho ? 25.0 / 384.0 : 0.0,
+                             g.ho ? 3.0 / 640.0 : 0.0};
+        for (int m = 0; m < 3; m++) {
+            g.derw[d][m] = w[m] / h[d];
+            g.derw32[d][m] = (float)g.derw[d][m];
+        }
+    }
+    g.hmin = fmin(h[0], fmin(h[1], h[2]));
+}
+
 // a grid constant in the precision R (the FP32 copy for float)
 template <typename R> __device__ __forceinline__ R gconst(double d, float f);
 template <> __device__ __forceinline__ double gconst<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float gconst<float>(double, float f) { return f; }
+
+// the DER weights of direction d in the precision R
+template <typename R> __device__ __forceinline__ const R *derw(const Grid &g, int d);
+template <> __device__ __forceinline__ const double *derw<double>(const Grid &g, int d)
+{
+    return g.derw[d];
+}
+template <> __device__ __forceinline__ const float *derw<float>(const Grid &g, int d)
+{
+    return g.derw32[d];
+}
 
 // a double in the precision R, rounded to nearest (integer pipe for float)
 template <typename R> __device__ __forceinline__ R to_r(double x);
@@ -165,6 +198,20 @@ __device__ __forceinline__ bool ltz(float x) { return x < 0.f; }
 __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
 __device__ __forceinline__ bool le(float a, float b) { return a <= b; }
 
+// 4 x, exact.  For a double the biased exponent field is stepped by 2 on the
+// integer pipe instead of spending an FP64-pipe multiply; valid for every x whose
+// exponent field lies in [1, 2044], i.e. every normal x with |x| < 2^1022.  Any
+// other x comes back unchanged: exact for zero, infinity and NaN, off by the factor
+// 4 for a subnormal x (|x| < 2.3e-308) and for |x| >= 2^1022, magnitudes that the
+// differences compared with the limiter's 1e-10 threshold never reach.
+__device__ __forceinline__ double times4(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    return e - 1u < 2044u ? __longlong_as_double(b + (2LL << 52)) : x;
+}
+__device__ __forceinline__ float times4(float x) { return 4.f * x; }
+
 template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return lt(a, b) ? a : b; }
 template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return lt(b, a) ? a : b; }
 
@@ -195,11 +242,11 @@ __device__ __forceinline__ bool mp5_smooth(R um2, R um1, R u0, R up1, R up2, R d
     // test reads (uor - u0)(uor - ump) <= eps with ump = u0 + minmod(dp, alpha (u0 - um1)),
     // so it needs only d = uor - u0, whose weights are the interpolant's with 1
     // taken from the centre one (90/128 - 1 = -38/128; all exact binary fractions)
-    const R alpha = R(4);
+    // (alpha = 4: the product alpha (u0 - um1) is times4)
     const R d = R(0.0234375) * um2 - R(0.15625) * um1 - R(0.296875) * u0 + R(0.46875) * up1 -
                 R(0.0390625) * up2;
     uor = u0 + d;
-    return le(d * (d - minmod2(dp, alpha * (u0 - um1))), R(1e-10));
+    return le(d * (d - minmod2(dp, times4(u0 - um1))), R(1e-10));
 }
 
 template <typename R>
@@ -364,6 +411,26 @@ __device__ __forceinline__ R der_c(const R *s, R inv_h, int ho)
     if (!ho) return (s[3] - s[2]) * inv_h;
     const R c0 = R(75.0 / 64.0), c1 = R(25.0 / 384.0), c2 = R(3.0 / 640.0);
     return (c0 * (s[3] - s[2]) - c1 * (s[4] - s[1]) + c2 * (s[5] - s[0])) * inv_h;
+}
+
+// acc - DER(s) and acc + DER(s) with the direction's weights w divided by h
+// (Grid::derw): the same stencil as der_c, each term one fused multiply-add.
+template <typename R>
+__device__ __forceinline__ R der_sub(R acc, const R *s, const R *w, int ho)
+{
+    acc = acc - w[0] * (s[3] - s[2]);
+    if (!ho) return acc;
+    acc = acc + w[1] * (s[4] - s[1]);
+    return acc - w[2] * (s[5] - s[0]);
+}
+
+template <typename R>
+__device__ __forceinline__ R der_add(R acc, const R *s, const R *w, int ho)
+{
+    acc = acc + w[0] * (s[3] - s[2]);
+    if (!ho) return acc;
+    acc = acc - w[1] * (s[4] - s[1]);
+    return acc + w[2] * (s[5] - s[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -604,7 +671,8 @@ __device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, con
         ok = c2p_eval(q, W, v2, r);
     }
     int it = 0;
-    bool conv = false, polish = false;
+    bool conv = false, polish = false, have_sq1 = false;
+    double sq1f = 0.0;
     while (ok && it < maxit) {
         double wb = W + q.B2;
         double iW = wb * r, iwb = W * r;
@@ -614,17 +682,41 @@ __device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, con
         double iW2 = iW * iW;
         double p = q.gm1g * (W * omv2 - q.D * sq1);
         double f = W - p + 0.5 * (1.0 + v2) * q.B2 - 0.5 * SB2 * iW2 - q.U;
-        double dW;
+        double dW, dv2 = 0.0;
+        if (!chord) dv2 = -2.0 * SB2 * (iW2 * iW) * iwb - 2.0 * v2 * iwb;
         if (chord) {
             dW = -f * idf;
         } else {
-            double dv2 = -2.0 * SB2 * (iW2 * iW) * iwb - 2.0 * v2 * iwb;
             double dp = q.gm1g * (omv2 - W * dv2 + 0.5 * q.D * dv2 * isq);
             double df = 1.0 - dp + 0.5 * q.B2 * dv2 + SB2 * (iW2 * iW);
             dW = -f / df;
         }
         if (!finite64(dW)) break;
         double lam = 1.0, Wn = W + dW, v2n, rn;
+        // Mixed path: the chord step that meets the stopping test moves W by at most
+        // tol W, so v^2, 1/(W (W + B^2)) and sqrt(1 - v^2) at the new point follow from
+        // their values and derivatives at W to second order in dW/W (below 1e-12
+        // relative, under the 1e-11 W error the chord stop leaves), in place of one
+        // more division and a square root.  A point that this leaves outside the
+        // domain takes the exact evaluation below.  (Newton's polishing step keeps the
+        // exact evaluation: its lanes reach it at different iterations, and a warp
+        // would run both forms.)
+        const bool last = chord && le(fabs(Wn - W), tol * Wn);
+        if (last) {
+            dv2 = -2.0 * SB2 * (iW2 * iW) * iwb - 2.0 * v2 * iwb;
+            v2n = v2 + dv2 * dW;
+            rn = r - (2.0 * W + q.B2) * (r * r) * dW;
+            if (gtz(Wn) && finite64(Wn) && finite64(v2n) && lt(v2n, 1.0) && gtz(rn)) {
+                it++;
+                sq1f = sq1 - 0.5 * isq * (v2n - v2);
+                have_sq1 = true;
+                W = Wn;
+                v2 = v2n;
+                r = rn;
+                conv = true;
+                break;
+            }
+        }
         bool okn = c2p_eval(q, Wn, v2n, rn);
         for (int k = 0; k < 60 && !okn; k++) {
             lam *= 0.5;
@@ -661,7 +753,7 @@ __device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, con
     Wout = W;
     if (!ok) v2 = fmin(fmax(v2, 0.0), 1.0);
     double omv2 = 1.0 - v2;
-    double sq1 = sqrt(omv2);
+    double sq1 = have_sq1 ? sq1f : sqrt(omv2);
     double p = q.gm1g * (W * omv2 - q.D * sq1);
     double rho = q.D * sq1;
     double wb = W + q.B2;

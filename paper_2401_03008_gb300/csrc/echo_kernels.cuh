@@ -361,7 +361,7 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
     int fs[6];
 #pragma unroll
     for (int m = 0; m < 6; m++) fs[m] = sidx<D>(g, (int)c, iD, m - 3);
-    const R ih = gconst<R>(g.inv_h[D], g.inv_h32[D]);
+    const R *w = derw<R>(g, D);
     const int ncomp = g.uct ? 5 : 8;
 #pragma unroll
     for (int q = 0; q < 8; q++) {
@@ -369,8 +369,7 @@ k_der(Grid g, const R *__restrict__ flux, R *__restrict__ rhs, int first, DevSca
         R s[6];
 #pragma unroll
         for (int m = 0; m < 6; m++) s[m] = ld(flux + q * n + (long)fs[m]);
-        R d = der_c(s, ih, g.ho);
-        rhs[q * n + c] = first ? -d : rhs[q * n + c] - d;
+        rhs[q * n + c] = der_sub(first ? R(0) : rhs[q * n + c], s, w, g.ho);
     }
 }
 
@@ -448,10 +447,11 @@ k_uct(Grid g, const R *__restrict__ Bf, const R *__restrict__ fda, const R *__re
     E[C * n + e] = uct_point(va, vb, Ba, Bb, apa, ama, apb, amb);
 }
 
-// curl of the edge field on the a-faces of cell (i,j,k): D_b E_c - D_c E_b
+// minus the curl of the edge field on the a-faces of cell (i,j,k), i.e. dB_a/dt:
+// D_c E_b - D_b E_c
 template <typename R>
-__device__ __forceinline__ R curl_a(const Grid &g, const R *__restrict__ E, int a, int i, int j,
-                                    int k)
+__device__ __forceinline__ R neg_curl_a(const Grid &g, const R *__restrict__ E, int a, int i,
+                                        int j, int k)
 {
     const int b = (a + 1) % 3, c = (a + 2) % 3;
     const long n = g.n;
@@ -461,8 +461,7 @@ __device__ __forceinline__ R curl_a(const Grid &g, const R *__restrict__ E, int 
         s[m] = ld(E + c * n + shifted_rt(g, i, j, k, b, m - 3));
         t[m] = ld(E + b * n + shifted_rt(g, i, j, k, c, m - 3));
     }
-    return der_c(s, gconst<R>(g.inv_h[b], g.inv_h32[b]), g.ho) -
-           der_c(t, gconst<R>(g.inv_h[c], g.inv_h32[c]), g.ho);
+    return der_add(der_sub(R(0), s, derw<R>(g, b), g.ho), t, derw<R>(g, c), g.ho);
 }
 
 // ---------------------------------------------------------------------------
@@ -489,7 +488,7 @@ k_rk(Grid g, int stage, int last, double a0, const R *__restrict__ E, const R *_
                 pu = U + v * n + c;
                 pu0 = U0 + v * n + c;
             } else {
-                r = g.uct ? -to_f64(curl_a(g, E, v - 5, i, j, k)) : to_f64(rhs[v * n + c]);
+                r = g.uct ? to_f64(neg_curl_a(g, E, v - 5, i, j, k)) : to_f64(rhs[v * n + c]);
                 pu = Bf + (v - 5) * n + c;
                 pu0 = Bf0 + (v - 5) * n + c;
             }
@@ -522,7 +521,7 @@ k_curl(Grid g, const R *__restrict__ E, double *__restrict__ out, double sign, i
     coords(g, c, i, j, k);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        double v = sign * to_f64(curl_a(g, E, a, i, j, k));
+        double v = -sign * to_f64(neg_curl_a(g, E, a, i, j, k));
         out[a * n + c] = accumulate ? out[a * n + c] + v : v;
     }
 }

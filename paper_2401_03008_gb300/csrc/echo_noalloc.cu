@@ -189,19 +189,17 @@ echo_status echo_diagnostics_noalloc(const double *cons5, const double *bface, i
     g.ny = ny;
     g.nz = nz;
     g.n = n;
-    g.h[0] = lx / nx;
-    g.h[1] = ly / ny;
-    g.h[2] = lz / nz;
-    for (int d = 0; d < 3; d++) g.inv_h[d] = 1.0 / g.h[d];
-    g.hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
     g.gam = 0.0;
     g.gfac = 0.0;
     g.gm1g = 0.0;
     g.gm1g32 = g.gam32 = g.gfac32 = 0.f;
-    for (int d = 0; d < 3; d++) g.inv_h32[d] = (float)g.inv_h[d];
     g.ho = ho;
     g.uct = 1;
     g.rec = 0;
+    {
+        const double h[3] = {lx / nx, ly / ny, lz / nz};
+        echo::set_spacing(g, h);
+    }
     g.lo[0] = g.lo[1] = g.lo[2] = 0;
     g.hi[0] = nx;
     g.hi[1] = ny;

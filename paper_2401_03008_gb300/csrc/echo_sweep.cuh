@@ -135,7 +135,7 @@ struct Mp5WarpQueue {
 // Segment sg covers cells [T sg, T sg + T) along D.  rhs: the cell right-hand side,
 // holding the x sweep's contribution (this kernel subtracts its DER).
 template <int D>
-__global__ void __launch_bounds__(SW_COLS, 4)
+__global__ void __launch_bounds__(SW_COLS, 5)
 k_sweep(Grid g, const __grid_constant__ CUtensorMap tm, const float *__restrict__ prim,
         const float *__restrict__ Bf, float *__restrict__ rhs, float *__restrict__ fd,
         DevScalars *sc, int T, int want_amax)
@@ -185,7 +185,7 @@ k_sweep(Grid g, const __grid_constant__ CUtensorMap tm, const float *__restrict_
     }
     __syncthreads();
     Mp5WarpQueue<14> &q = wq[warp];
-    const float gam = g.gam32, gfac = g.gfac32, ih = g.inv_h32[D];
+    const float gam = g.gam32, gfac = g.gfac32, *w = g.derw32[D];
     float Fh[6][5];  // fluxes of faces f-5..f of this column
     float amax = 0.f;
     unsigned nfb = 0;
@@ -308,7 +308,7 @@ k_sweep(Grid g, const __grid_constant__ CUtensorMap tm, const float *__restrict_
                 for (int qq = 0; qq < 5; qq++) {
                     const float s6[6] = {Fh[0][qq], Fh[1][qq], Fh[2][qq],
                                          Fh[3][qq], Fh[4][qq], Fh[5][qq]};
-                    rhs[qq * n + cc] -= der_c(s6, ih, g.ho);
+                    rhs[qq * n + cc] = der_sub(rhs[qq * n + cc], s6, w, g.ho);
                 }
             }
         }
