@@ -73,16 +73,20 @@ enum { ECHO_FP64 = 0, ECHO_MIXED = 1 };
  * small learned network loaded with echo_mlp_load (falls back to the previous W
  * where its guess is unusable). */
 enum { ECHO_GUESS_PREV = 0, ECHO_GUESS_COLD = 1, ECHO_GUESS_MLP = 2 };
-/* Kernels of the mixed path's y and z sweeps (Sec. 3 steps 2-3).  The fused kernel
- * stages planes of the primitives in shared memory by TMA and keeps the face fluxes
- * on chip (REC, fluxes, HLL and DER in one pass); the separate kernels write the
- * fluxes of one direction and take their DER in a second kernel.  Both compute the
- * same arithmetic per face, compiled apart, so they agree to FP32 rounding, not bit
- * for bit.  ECHO_SWEEPS_AUTO: fused where it pays (grids of at least four waves of
- * blocks); ECHO_SWEEPS_FUSED: fused wherever the grid allows it; ECHO_SWEEPS_SEPARATE:
- * never.  The fused kernel needs UCT, MP5 and nx a multiple of 4 (rows of 16-byte
- * multiples for TMA), and at least 8 cells along the direction; elsewhere, and on
- * the FP64 path, the separate kernels run. */
+/* Kernels of the mixed path's substep (Sec. 3 steps 1-3).  Along y and z the fused
+ * kernel stages planes of the primitives in shared memory by TMA and keeps the face
+ * fluxes on chip (REC, fluxes, HLL and DER in one pass); along x the fused kernel
+ * is the inversion (INT + C2P) of a row of cells followed by the row's REC, fluxes,
+ * HLL and DER from shared memory.  The separate kernels invert every cell, then
+ * write the fluxes of one direction and take their DER in a second kernel.  Both
+ * compute the same arithmetic per cell and face, compiled apart, so they agree to
+ * FP32 rounding, not bit for bit.  ECHO_SWEEPS_AUTO: fused where it pays (grids of
+ * at least four waves of blocks); ECHO_SWEEPS_FUSED: fused wherever the grid allows
+ * it; ECHO_SWEEPS_SEPARATE: never.  The fused kernels need UCT and MP5; the y/z one
+ * also nx a multiple of 4 (rows of 16-byte multiples for TMA) and at least 8 cells
+ * along its direction, the x one 8 <= nx <= 1024.  The x one is not used with the
+ * learned guess or a harvest.  Elsewhere, and on the FP64 path, the separate kernels
+ * run. */
 enum { ECHO_SWEEPS_AUTO = 0, ECHO_SWEEPS_FUSED = 1, ECHO_SWEEPS_SEPARATE = 2 };
 
 typedef struct {
@@ -103,7 +107,7 @@ typedef struct {
     int device;         /* CUDA device ordinal */
     void *stream;       /* cudaStream_t to launch on; NULL: the library makes one */
     int rk_order;       /* 3: SSP-RK3 (default); 2: SSP-RK2 (the faster variant of Sec. 4) */
-    int sweeps;         /* ECHO_SWEEPS_*: the mixed path's y and z sweep kernels */
+    int sweeps;         /* ECHO_SWEEPS_*: the mixed path's fused or separate sweep kernels */
 } echo_config;
 
 /* Fill *cfg with defaults: 32^3 unit box, gamma 4/3, cfl 0.4, uct 1, ho 1, MP5,

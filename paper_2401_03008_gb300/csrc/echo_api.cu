@@ -15,7 +15,7 @@ namespace {
 const char *kKernelNames[ECHO_NKERNELS] = {
     "int_c2p", "flux_x", "flux_y", "flux_z", "der_x", "der_y", "der_z", "uct_x",
     "uct_y", "uct_z", "rk_curl", "dt", "curl", "init", "diag", "misc", "mlp_guess",
-    "sweep_y", "sweep_z", "unused19"};
+    "sweep_y", "sweep_z", "c2p_sweep_x"};
 
 char g_err[256] = "no error";
 
@@ -349,15 +349,17 @@ void launch_stage(echo_ctx *c, int stage, Harvest *hv)
     // the learned guess: everywhere when selected, else for the first inversion after
     // a resume without a stored W (when the weights are loaded)
     const bool learned = c->cfg.c2p_guess == ECHO_GUESS_MLP || (stage == 1 && c->w_cold);
-    Path<R>::int_c2p(c, stage, 1, learned);
-    if (stage == 1) c->w_cold = false;
     if (hv) {
+        Path<R>::int_c2p(c, stage, 1, learned);
         long off = (hv->calls * 7919L) % hv->stride;
         hv->count += echo::launch_mlp_harvest(c, hv->stride, off, hv->feats, hv->target,
                                               hv->count, hv->capacity);
         hv->calls++;
+        Path<R>::sweeps(c, stage == 1);
+    } else {
+        Path<R>::c2p_sweeps(c, stage, learned, stage == 1);
     }
-    Path<R>::sweeps(c, stage == 1);
+    if (stage == 1) c->w_cold = false;
     if (stage == 1) echo::launch_dt(c);
     Path<R>::uct(c);
     Path<R>::rk(c, stage);
@@ -522,8 +524,7 @@ echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *am
     const bool learned = c->cfg.c2p_guess == ECHO_GUESS_MLP || c->w_cold;
     c->w_cold = false;
     if (c->mixed) {
-        Path<float>::int_c2p(c, 0, 1, learned);
-        Path<float>::sweeps(c, 1);
+        Path<float>::c2p_sweeps(c, 0, learned, 1);
         Path<float>::uct(c);
         if (c->g.uct) {
             if (df) Path<float>::curl_out(c, df);
@@ -532,8 +533,7 @@ echo_status echo_rhs(echo_ctx *c, double *rhs_cons, double *rhs_face, double *am
             Path<float>::rhs_out(c, tmp8);
         }
     } else {
-        Path<double>::int_c2p(c, 0, 1, learned);
-        Path<double>::sweeps(c, 1);
+        Path<double>::c2p_sweeps(c, 0, learned, 1);
         Path<double>::uct(c);
         if (c->g.uct) {
             if (df) Path<double>::curl_out(c, df);

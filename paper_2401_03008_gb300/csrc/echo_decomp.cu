@@ -232,8 +232,7 @@ void substep(echo_decomp *d, int stage)
 {
     exchange(d);
     for (echo_ctx *c : d->sub) {
-        echo::Path<R>::int_c2p(c, stage, 1, false);
-        echo::Path<R>::sweeps(c, stage == 1);
+        echo::Path<R>::c2p_sweeps(c, stage, false, stage == 1);
     }
     if (stage == 1) echo::launch_dt(d->sub[0]);
     for (echo_ctx *c : d->sub) {

@@ -16,7 +16,7 @@ namespace echo {
 enum Kind {
     K_C2P = 0, K_FLUX_X, K_FLUX_Y, K_FLUX_Z, K_DER_X, K_DER_Y, K_DER_Z,
     K_UCT_X, K_UCT_Y, K_UCT_Z, K_RK, K_DT, K_CURL, K_INIT, K_DIAG, K_MISC, K_MLP,
-    K_SWEEP_Y, K_SWEEP_Z
+    K_SWEEP_Y, K_SWEEP_Z, K_C2P_X
 };
 
 struct ProfRec {
@@ -66,6 +66,8 @@ struct echo_ctx {
     // separate flux and DER kernels)
     CUtensorMap tm_prim[3];
     int sweep_T[3];
+    // mixed path: the inversion and the x sweep as one kernel (k_c2p_xsweep)
+    bool xsweep;
     std::vector<echo::ProfRec> prof;
     long prof_count[ECHO_NKERNELS];
     double prof_ms[ECHO_NKERNELS];
@@ -121,8 +123,13 @@ struct Path {
     static void int_c2p(echo_ctx *c, int stage, int update_w, bool learned);
     // the learned guesses of the current state into c->guess (echo_mlp_guess)
     static void mlp_guess(echo_ctx *c);
-    // sweeps + DER (steps 2-3), want_amax on the first stage of a step
-    static void sweeps(echo_ctx *c, int want_amax);
+    // sweeps + DER (steps 2-3), want_amax on the first stage of a step; with_x = 0
+    // leaves out the x sweep (done with the inversion by k_c2p_xsweep)
+    static void sweeps(echo_ctx *c, int want_amax, int with_x = 1);
+    // INT + C2P (updating W) and the sweeps of one substep: on the mixed path the
+    // inversion and the x sweep as one kernel where the context chose it (not with
+    // the learned guess), else int_c2p then sweeps
+    static void c2p_sweeps(echo_ctx *c, int stage, bool learned, int want_amax);
     // UCT edge fields (step 4, first half)
     static void uct(echo_ctx *c);
     // RK stage with the curl of E (step 4, second half, and step 5)
@@ -157,6 +164,8 @@ void drop_step_graph(echo_ctx *c);
 void make_sweep_maps(echo_ctx *c);
 // mixed path: the fused reconstruction + flux + DER sweep along D = 1, 2
 void launch_fused_sweep(echo_ctx *c, int D, int want_amax);
+// mixed path: INT + C2P fused with the x sweep (c->xsweep)
+void launch_c2p_xsweep(echo_ctx *c, int stage, int want_amax);
 // harvest of training states (features, converged W/U) of cells offset + q stride
 // into slots base + q (those below capacity); returns the number of such cells
 long launch_mlp_harvest(echo_ctx *c, long stride, long offset, float *feats, float *target,

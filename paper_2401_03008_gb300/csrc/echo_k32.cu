@@ -1,10 +1,12 @@
 // FP32 instantiation of the substep kernels (the mixed-precision path: single
-// precision reconstruction, fluxes, DER and constrained transport), and the fused
-// y/z sweeps of that path with their TMA descriptors.
+// precision reconstruction, fluxes, DER and constrained transport), the fused y/z
+// sweeps of that path with their TMA descriptors, and its inversion fused with the
+// x sweep.
 #include <cudaTypedefs.h>
 
 #include "echo_kernels.cuh"
 #include "echo_sweep.cuh"
+#include "echo_xsweep.cuh"
 
 namespace echo {
 
@@ -55,12 +57,22 @@ void make_sweep_maps(echo_ctx *c)
 {
     const Grid &g = c->g;
     c->sweep_T[0] = c->sweep_T[1] = c->sweep_T[2] = 0;
+    c->xsweep = false;
     const int mode = c->cfg.sweeps;
-    if (mode == ECHO_SWEEPS_SEPARATE || !g.uct || g.rec != 0 || g.nx % 4 != 0) return;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    if (!enc) return;
+    if (mode == ECHO_SWEEPS_SEPARATE || !g.uct || g.rec != 0) return;
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->cfg.device);
+    // the inversion fused with the x sweep: rows of 8 to XS_NXMAX cells; automatic
+    // where the rows give four waves of three blocks per SM
+    if (g.nx >= 8 && g.nx <= XS_NXMAX &&
+        (mode == ECHO_SWEEPS_FUSED || (long)g.ny * g.nz >= 12L * nsm) &&
+        cudaFuncSetAttribute(k_c2p_xsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)xs_smem_bytes(XS_NXMAX)) == cudaSuccess)
+        c->xsweep = true;
+    cudaGetLastError();
+    if (g.nx % 4 != 0) return;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return;
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 8};
     const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4,
                                    (cuuint64_t)g.n * 4};
@@ -93,6 +105,17 @@ void launch_fused_sweep(echo_ctx *c, int D, int want_amax)
         launch(c, K_SWEEP_Z, k_sweep<2>, blocks, SW_COLS, 0, g, c->tm_prim[2],
                (const float *)c->prim, (const float *)c->Bf32, (float *)c->rhs, fd, c->sc, T,
                want_amax);
+}
+
+void launch_c2p_xsweep(echo_ctx *c, int stage, int want_amax)
+{
+    const Grid &g = c->g;
+    C2PParams par{c->cfg.c2p_tol, c->cfg.c2p_maxit, c->cfg.c2p_guess, 1};
+    if (par.guess == ECHO_GUESS_MLP) par.guess = ECHO_GUESS_PREV;
+    launch(c, K_C2P_X, k_c2p_xsweep, (unsigned)((long)g.ny * g.nz), XS_BS, xs_smem_bytes(g.nx),
+           g, (const double *)c->U, (const double *)c->Bf, c->W, (float *)c->prim,
+           (const float *)c->Bf32, (float *)c->rhs, (float *)c->fdat[0], par, c->sc, stage,
+           want_amax);
 }
 
 }  // namespace echo

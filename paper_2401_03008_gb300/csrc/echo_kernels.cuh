@@ -579,7 +579,19 @@ unsigned Path<R>::mlp_grid(echo_ctx *c)
 }
 
 template <typename R>
-void Path<R>::sweeps(echo_ctx *c, int want_amax)
+void Path<R>::c2p_sweeps(echo_ctx *c, int stage, bool learned, int want_amax)
+{
+    if (sizeof(R) == 4 && c->xsweep && !(learned && c->mlp_w)) {
+        launch_c2p_xsweep(c, stage, want_amax);
+        sweeps(c, want_amax, 0);
+    } else {
+        int_c2p(c, stage, 1, learned);
+        sweeps(c, want_amax, 1);
+    }
+}
+
+template <typename R>
+void Path<R>::sweeps(echo_ctx *c, int want_amax, int with_x)
 {
     const Grid &g = c->g;
     const unsigned nb0 = tile_blocks<flux_map(0)>(g), nb1 = tile_blocks<flux_map(1)>(g),
@@ -589,9 +601,11 @@ void Path<R>::sweeps(echo_ctx *c, int want_amax)
     const R *prim = (const R *)c->prim;
     const R *bf = face_field<R>(c);
     R *flux = (R *)c->flux, *rhs = (R *)c->rhs;
-    launch(c, K_FLUX_X, k_flux<R, 0>, nb0, BS, 0, g, prim, bf, flux,
-           (R *)c->fdat[0], c->sc, want_amax);
-    launch(c, K_DER_X, k_der<R, 0>, nd0, BS, 0, g, (const R *)flux, rhs, 1, c->sc);
+    if (with_x) {
+        launch(c, K_FLUX_X, k_flux<R, 0>, nb0, BS, 0, g, prim, bf, flux,
+               (R *)c->fdat[0], c->sc, want_amax);
+        launch(c, K_DER_X, k_der<R, 0>, nd0, BS, 0, g, (const R *)flux, rhs, 1, c->sc);
+    }
     // mixed path: y and z as fused sweeps where chosen (TMA-staged planes, the face
     // fluxes kept on chip), else the flux kernel and its DER
     if (sizeof(R) == 4 && c->sweep_T[1]) {

@@ -212,9 +212,14 @@ def test_c2p_failure_rolls_back():
     assert t1 == t0 and step1 == step0
 
 
-def test_unphysical_state_reported():
+@pytest.mark.parametrize("kw", [dict(), dict(precision="mixed", sweeps="fused"),
+                                dict(precision="mixed", sweeps="separate")])
+def test_unphysical_state_reported(kw):
+    """A cell whose energy lies below its rest mass: every inversion kernel (the
+    mixed path's inversion fused with the x sweep included) reports it, and the step
+    is rolled back."""
     n = (12, 10, 8)
-    s = echo.Solver(*n)
+    s = echo.Solver(*n, **kw)
     s.set_state(*smooth(n, 36))
     cons, bf, w, t, step = s.get_state()
     cons[4, 3, 2, 1] = 0.1 * cons[0, 3, 2, 1]  # energy below the rest mass
