@@ -35,10 +35,10 @@ SEED = 2401_03008
 
 # Algorithmic per-unit costs of each kernel kind: one unit is one cell, face or edge
 # of the launch.  Bytes: each array element read or written once (stencil
-# neighbours come from cache).  FLOPs: FP64 (or FP32 in the mixed path)
-# floating-point operations the algorithm performs per unit, an FMA counted as 2,
-# as counted by ncu (sass thread instructions, FP64 add/mul/fma) at 96^3 and read
-# from profiles/flops_per_unit.json.
+# neighbours come from cache).  FLOPs: FP64 (or FP32 for the mixed path's FP32
+# kernels) floating-point operations the kernel performs per unit, an FMA counted
+# as 2, as counted by ncu (sass thread instructions, add/mul/fma) on the 192^3
+# turbulence and read from profiles/flops_per_unit.json.
 R64, R32 = 8, 4
 
 
@@ -50,7 +50,17 @@ def bytes_per_unit(kind, r):
         "der_x": 5 * r + 5 * r, "der_y": 5 * r + 10 * r, "der_z": 5 * r + 10 * r,
         "uct_x": 8 * r + 16 + r, "uct_y": 8 * r + 16 + r, "uct_z": 8 * r + 16 + r,
         "rk_curl": 5 * r + 3 * r + 3 * 64,
+        # mixed path: the inversion fused with the x sweep (U, B faces, W in and out,
+        # the normal field; primitives, rhs and UCT face data out) and the fused y/z
+        # sweeps (primitives and the normal field in, rhs read and written, face data)
+        "c2p_sweep_x": 5 * 8 + 3 * 8 + 2 * 8 + r + 8 * r + 5 * r + 6 * r,
+        "sweep_y": 8 * r + r + 10 * r + 6 * r, "sweep_z": 8 * r + r + 10 * r + 6 * r,
     }.get(kind)
+
+
+# kernels bound by the FP64 pipe on the mixed path (the inversion and the RK
+# accumulation stay FP64); every kernel of the FP64 path is
+FP64_BOUND = ("int_c2p", "c2p_sweep_x", "rk_curl")
 
 
 FLOPS_PER_UNIT = {}  # filled from the ncu counts (profiles/), kernel -> flops per unit
@@ -413,8 +423,8 @@ def roofline_and_profile(args, s, n):
     if os.path.exists(pk):
         peaks = _json.load(open(pk))
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    fp = "fp64" if args.precision == "fp64" else "fp32"
-    alu_peak = s.probe_fma_peak("fp64" if top == "int_c2p" or fp == "fp64" else "fp32")
+    fp = "fp64" if args.precision == "fp64" or top in FP64_BOUND else "fp32"
+    alu_peak = s.probe_fma_peak(fp)
     r = R64 if args.precision == "fp64" else R32
     units = n ** 3
     flops_tab = load_flops_table().get(args.precision, {})
@@ -427,7 +437,7 @@ def roofline_and_profile(args, s, n):
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / (alu_peak / 1e12),
                 "peak_source": "measured FMA-chain probe (%s vector)" %
-                               ("FP64" if fp == "fp64" or top == "int_c2p" else "FP32")}
+                               ("FP64" if fp == "fp64" else "FP32")}
     else:
         achieved = bpu * units / per_launch_s / 1e9 if bpu else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -436,15 +446,16 @@ def roofline_and_profile(args, s, n):
     roof.update({"kernel": top, "traffic": None, "launch_ms": per_launch_s * 1e3,
                  "share": kms / tot, "hbm_gbs_algorithmic": (bpu * units / per_launch_s / 1e9
                                                              if bpu else None)})
-    tr = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
+    tr = os.path.join(ROOT, "profiles", "traffic_per_unit.json")
     if os.path.exists(tr):
         tab = _json.load(open(tr))
-        key = args.workload if args.workload in tab else None
-        tt = tab.get(key, {}).get(args.precision, {}).get(top) if key else None
+        tt = tab.get(args.workload, {}).get(args.precision, {}).get(top)
         if tt:
             # measured DRAM bytes per unit (ncu on a smaller grid of the same workload,
             # every array far larger than L2) times the units of one launch
             roof["traffic"] = tt * units
+            roof["traffic_source"] = ("ncu dram__bytes_read + dram__bytes_write per unit on "
+                                      "the 192^3 grid of the workload, times the launch's units")
 
     fp64_peak = s.probe_fma_peak("fp64")
     fp32_peak = s.probe_fma_peak("fp32")

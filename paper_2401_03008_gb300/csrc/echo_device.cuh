@@ -642,7 +642,9 @@ __device__ __forceinline__ C2PInv c2p_invariants(const double *u, const double *
 
 // Wfb: a second starting point, taken when W0 lies outside the domain (the
 // previous W when W0 is the learned guess; *fb reports that it was taken); pass
-// fb = nullptr for none.
+// fb = nullptr for none.  MIXED: compile the mixed path's FP32 pre-iterations and
+// chord steps (taken when pre32 != 0); the FP64 path's kernels leave them out.
+template <bool MIXED>
 __device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, const double *B,
                                            double W0, double tol, int maxit, double *prim,
                                            double &Wout, int &iters, int pre32, int &iters32,
@@ -654,8 +656,8 @@ __device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, con
     // FP64 step (a chord iteration: FP64 residual, FP32-accurate slope, contraction
     // by about the slope's relative error per step), so an FP64 step evaluates f only
     float idf32 = 0.f;
-    if (pre32) W0 = c2p_pre32(q, W0, iters32, idf32);
-    const bool chord = idf32 != 0.f;
+    if (MIXED && pre32) W0 = c2p_pre32(q, W0, iters32, idf32);
+    const bool chord = MIXED && idf32 != 0.f;
     const double idf = to_f64(idf32);
     double W = W0, v2 = 0.0, r = 0.0;
     bool ok = c2p_eval(q, W, v2, r);
@@ -770,7 +772,8 @@ __device__ __forceinline__ bool c2p_newton(const double *u, const double *B, dou
                                            int &iters32)
 {
     const C2PInv q = c2p_invariants(u, B, gm1g, gm1g32);
-    return c2p_newton(q, u, B, W0, tol, maxit, prim, Wout, iters, pre32, iters32);
+    return pre32 ? c2p_newton<true>(q, u, B, W0, tol, maxit, prim, Wout, iters, pre32, iters32)
+                 : c2p_newton<false>(q, u, B, W0, tol, maxit, prim, Wout, iters, pre32, iters32);
 }
 
 // ---------------------------------------------------------------------------

@@ -97,10 +97,10 @@ __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
 // through L1); a guess that is unusable falls back to the previous W and is counted.
 // The network runs on whole warps, before the divergent Newton iteration: lanes
 // past the grid evaluate it on a placeholder state.
-// The network variant asks for the same three blocks on the FP64 path (the cell's
-// state is spilled across the network and reloaded, cheaper than a block less);
-// the FP32 path takes two blocks rather than spill more.
-constexpr int minb_c2p_mlp(int rbytes) { return rbytes == 4 ? 2 : 3; }
+// The network variant takes two blocks per SM (128 registers, no spills) on both
+// paths: on a resume of the 128^3 turbulence its FP64 inversion took 1.25 ms with
+// two blocks against 1.27 ms with three (spilling), the cold start 1.39 ms.
+constexpr int minb_c2p_mlp(int) { return 2; }
 
 template <typename R, bool MLP>
 __global__ void __launch_bounds__(BS, MLP ? minb_c2p_mlp(sizeof(R)) : minb_c2p(sizeof(R)))
@@ -146,8 +146,10 @@ k_int_c2p(Grid g, const double *__restrict__ U, const double *__restrict__ Bf,
         else W0 = W[c];
         double p[5], Wn;
         int iters, iters32;
-        bad = !c2p_newton(q, u, B, W0, par.tol, par.maxit, p, Wn, iters, par.pre32, iters32, Wfb,
-                          MLP ? &fb : nullptr);
+        // the FP32 pre-iterations and chord steps are compiled into the mixed path's
+        // kernels only
+        bad = !c2p_newton<sizeof(R) == 4>(q, u, B, W0, par.tol, par.maxit, p, Wn, iters,
+                                          par.pre32, iters32, Wfb, MLP ? &fb : nullptr);
         it = (unsigned)iters;
         it32 = (unsigned)iters32;
 #pragma unroll

@@ -195,6 +195,17 @@ k_sweep(Grid g, const __grid_constant__ CUtensorMap tm, const float *__restrict_
     bool ok0 = true;
     for (int lq = 0; lq < 5; lq++) ok0 &= mbar_wait(&bars[lq], 0u);
     for (int f = k0 - 3; f <= kend + 1; f++) {
+        // global loads that do not depend on the planes go first, so that their latency
+        // overlaps the wait and the reconstruction: the normal field of face f and the
+        // right-hand side of cell f - 2, whose DER follows this face
+        const long fc = cbase + (long)wrapD(f) * strideD;  // face f belongs to cell f
+        const float bn = active ? Bf[D * n + fc] : 0.f;
+        const int kc = f - 2;
+        const bool derc = active && kc >= k0 && kc < kend;
+        const long cc = cbase + (long)kc * strideD;
+        float rh[5];
+#pragma unroll
+        for (int qq = 0; qq < 5; qq++) rh[qq] = derc ? rhs[qq * n + cc] : 0.f;
         const int lp = f + 3 - p0;  // the plane f + 3 completes the stencil of face f
         const bool ok = mbar_wait(&bars[lp & (SW_RING - 1)], (unsigned)(lp >> 3) & 1u) && ok0;
         // every thread is past face f - 1 here, so plane f - 3's slot is free
@@ -246,8 +257,6 @@ k_sweep(Grid g, const __grid_constant__ CUtensorMap tm, const float *__restrict_
             if (mask & (1u << kl)) L[v] = q.get(kl, lane);
             if (mask & (1u << (kl + 1))) R[v] = q.get(kl + 1, lane);
         }
-        const long fc = cbase + (long)wrapD(f) * strideD;  // face f belongs to cell f
-        const float bn = active ? Bf[D * n + fc] : 0.f;
         L[5 + D] = bn;
         R[5 + D] = bn;
         // positivity: a state with rho <= 0, p <= 0 or v^2 >= 1 takes the cell value
@@ -301,14 +310,12 @@ k_sweep(Grid g, const __grid_constant__ CUtensorMap tm, const float *__restrict_
                     amax = fmaxf(amax, fmaxf(ap, am));
             }
             // DER of cell f - 2 from faces f-5 .. f
-            const int kc = f - 2;
-            if (kc >= k0 && kc < kend) {
-                const long cc = cbase + (long)kc * strideD;
+            if (derc) {
 #pragma unroll
                 for (int qq = 0; qq < 5; qq++) {
                     const float s6[6] = {Fh[0][qq], Fh[1][qq], Fh[2][qq],
                                          Fh[3][qq], Fh[4][qq], Fh[5][qq]};
-                    rhs[qq * n + cc] = der_sub(rhs[qq * n + cc], s6, w, g.ho);
+                    rhs[qq * n + cc] = der_sub(rh[qq], s6, w, g.ho);
                 }
             }
         }

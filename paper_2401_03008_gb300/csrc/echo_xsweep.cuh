@@ -17,6 +17,7 @@
 #pragma once
 
 #include "echo_kernels.cuh"
+#include "echo_sweep.cuh"
 
 namespace echo {
 
@@ -38,10 +39,9 @@ k_c2p_xsweep(Grid g, const double *__restrict__ U, const double *__restrict__ Bf
              int stage, int want_amax)
 {
     extern __shared__ __align__(16) float xs[];  // P[8][nx], F[5][nx]
-    __shared__ Mp5Queue<float, 16, QMAX, BS> q;
+    __shared__ Mp5WarpQueue<14> wq[XS_BS / 32];
     __shared__ float red[XS_BS / 32];
     __shared__ int halted;
-    static_assert(XS_BS == BS, "the limiting queue is sized for BS threads");
     // the flag may be raised by another block of this launch: read it once, so that
     // the whole block leaves or stays (the phases have block barriers)
     if (threadIdx.x == 0) halted = *(volatile int *)&sc->halt;
@@ -66,7 +66,7 @@ k_c2p_xsweep(Grid g, const double *__restrict__ U, const double *__restrict__ Bf
         const double W0 = par.guess == 1 ? u[4] : W[c];
         double p[5], Wn;
         int iters, iters32;
-        const bool bad = !c2p_newton(qi, u, B, W0, par.tol, par.maxit, p, Wn, iters, par.pre32,
+        const bool bad = !c2p_newton<true>(qi, u, B, W0, par.tol, par.maxit, p, Wn, iters, par.pre32,
                                      iters32);
 #pragma unroll
         for (int v = 0; v < 5; v++) {
@@ -113,37 +113,42 @@ k_c2p_xsweep(Grid g, const double *__restrict__ U, const double *__restrict__ Bf
     const float gam = g.gam32, gfac = g.gfac32;
     float amax = 0.f;
     unsigned nfb = 0;
+    // The deferred MP5 limiting runs per warp (warp-synchronous queue, no block
+    // barrier); every lane reconstructs, a lane past the row on the row's last face.
+    Mp5WarpQueue<14> &q = wq[tid >> 5];
     for (int base = 0; base < nx; base += XS_BS) {
-        q.reset();
-        __syncthreads();
-        const int i = base + tid;
-        const bool active = i < nx;
+        const int i0 = base + tid;
+        const bool active = i0 < nx;
+        const int i = active ? i0 : nx - 1;
         int cs[6];
         float L[8], Rt[8];
         unsigned mask = 0;
-        if (active) {
+        int cnt = 0;
 #pragma unroll
-            for (int m = 0; m < 6; m++) cs[m] = xs_wrap(i + m - 2, nx);
+        for (int m = 0; m < 6; m++) cs[m] = xs_wrap(i + m - 2, nx);
 #pragma unroll
-            for (int v = 0; v < 8; v++) {
-                if (v == 5) continue;  // the normal field is the staggered face value
-                float s[6];
+        for (int v = 0; v < 8; v++) {
+            if (v == 5) continue;  // the normal field is the staggered face value
+            const int kl = 2 * v - (v > 5 ? 2 : 0);
+            float s[6];
 #pragma unroll
-                for (int m = 0; m < 6; m++) s[m] = P[v * nx + cs[m]];
-                const float dc = s[3] - s[2];  // shared by both states of the face
-                L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], dc, 2 * v, mask);
-                Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], -dc, 2 * v + 1, mask);
-            }
+            for (int m = 0; m < 6; m++) s[m] = P[v * nx + cs[m]];
+            const float dc = s[3] - s[2];  // shared by both states of the face
+            L[v] = q.defer(s[0], s[1], s[2], s[3], s[4], dc, kl, mask, lane, cnt);
+            Rt[v] = q.defer(s[5], s[4], s[3], s[2], s[1], -dc, kl + 1, mask, lane, cnt);
         }
-        __syncthreads();
-        q.process();
-        __syncthreads();
-        if (active) {
+        __syncwarp();
+        q.process(lane, cnt);
+        __syncwarp();
 #pragma unroll
-            for (int v = 0; v < 8; v++) {
-                if (mask & (1u << (2 * v))) L[v] = q.get(2 * v);
-                if (mask & (1u << (2 * v + 1))) Rt[v] = q.get(2 * v + 1);
-            }
+        for (int v = 0; v < 8; v++) {
+            if (v == 5) continue;
+            const int kl = 2 * v - (v > 5 ? 2 : 0);
+            if (mask & (1u << kl)) L[v] = q.get(kl, lane);
+            if (mask & (1u << (kl + 1))) Rt[v] = q.get(kl + 1, lane);
+        }
+        __syncwarp();  // the queue of this batch is read before the next batch's entries
+        if (active) {
             const long f = row + i;
             const float bn = Bf32[f];
             L[5] = bn;
