@@ -302,6 +302,9 @@ def main():
                          "Sec. 5; 7: 2 x 2 x 2 blocks with the wide halo against one grid; "
                          "8: time to accuracy of the FP64 and mixed paths on the Alfven wave")
     ap.add_argument("--config-steps", type=int, default=20)
+    ap.add_argument("--config-runs", default="",
+                    help="configs 4-5: comma list of precision_guess runs to keep "
+                         "(e.g. mixed_prev,mixed_mlp); default all")
     ap.add_argument("--config5-n", type=int, default=768)
     ap.add_argument("--config5-steps", type=int, default=200)
     ap.add_argument("--config5-lorentz-max", type=float, default=3.5,
@@ -712,6 +715,9 @@ def run_config(args):
         runs = ([("fp64", "prev"), ("fp64", "cold"), ("fp64", "mlp"), ("mixed", "prev"),
                  ("mixed", "cold"), ("mixed", "mlp")] if args.config == 4 else
                 [("fp64", "prev"), ("mixed", "prev"), ("mixed", "mlp")])
+        if args.config_runs:
+            keep_runs = set(args.config_runs.split(","))
+            runs = [r for r in runs if "%s_%s" % r in keep_runs]
         ref, ref_steps = None, None
         for prec, guess in runs:
             steps = args.config_steps if args.config == 4 else args.config5_steps
