@@ -463,6 +463,31 @@ def test_mixed_sweep_kernels_against_oracle(sweeps):
             assert np.mean(np.abs(p[v] - ref[v])) / scale < 1e-6, (sweeps, v)
 
 
+@pytest.mark.parametrize("n", [(8, 12, 10), (1024, 4, 3), (1032, 4, 3)])
+def test_row_kernel_at_its_limits(n):
+    """The mixed path's inversion fused with the x sweep holds a whole row in shared
+    memory: the shortest and the longest row it takes (8 and 1024 cells) against the
+    oracle, and one cell more than it takes, where the separate kernels run."""
+    L = (1.0, 0.5, 0.4)
+    g, s = make_pair(n, L=L, precision="mixed", sweeps="fused", state=smooth(n, 44, L=L))
+    cons0 = g.cons.copy()
+    rc, rb, amax, bad = g.rhs()
+    s.profile(True)
+    s.profile_read(reset=True)
+    grc, grb, gamax = s.rhs()
+    prof = s.profile_read(reset=True)
+    fused = n[0] <= 1024
+    assert (prof.get("c2p_sweep_x", (0, 0.0))[0] == 1) == fused, prof
+    assert (prof.get("int_c2p", (0, 0.0))[0] == 1) == (not fused), prof
+    assert gamax == pytest.approx(amax, rel=1e-6)
+    hmin = min(L[d] / n[d] for d in range(3))
+    for got, ref, q, groups in ((grc, rc, cons0, CONS_GROUPS), (grb, rb, g.bf, FACE_GROUPS)):
+        for grp in groups:
+            floor = np.max(np.abs(q[grp])) * amax / hmin
+            assert_parity(got[grp], ref[grp], [list(range(len(grp)))], tol=2e-6, floor=floor,
+                          what="mixed rhs, rows of %d" % n[0])
+
+
 def test_fused_sweep_agrees_with_separate_and_repeats_bit_for_bit():
     """The turbulence at its full amplitude on 96^3, where most warps limit some
     reconstructions: the fused sweep gives the separate kernels' right-hand side to
