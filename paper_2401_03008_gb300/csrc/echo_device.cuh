@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "echo_convert.cuh"
+#include "echo_mp5dec.cuh"
 
 namespace echo {
 
@@ -246,6 +247,14 @@ __device__ __forceinline__ bool mp5_smooth(R um2, R um1, R u0, R up1, R up2, R d
     const R d = R(0.0234375) * um2 - R(0.15625) * um1 - R(0.296875) * u0 + R(0.46875) * up1 -
                 R(0.0390625) * up2;
     uor = u0 + d;
+    if constexpr (sizeof(R) == 8) {
+        // FP64 path: the test in FP32 with its error bound (echo_mp5dec.cuh); FP64
+        // only where that cannot decide (about 1e-4 of the tests on the turbulence).
+        // up1 - u0 is the caller's dp to the bit (the mirrored state passes -dp).
+        const int r = mp5_test32(d, um1, u0, up1);
+        if (r >= 0) return r != 0;
+        return le(d * (d - minmod2(up1 - u0, times4(u0 - um1))), R(1e-10));
+    }
     return le(d * (d - minmod2(dp, times4(u0 - um1))), R(1e-10));
 }
 
