@@ -213,6 +213,38 @@ __device__ __forceinline__ double times4(double x)
 }
 __device__ __forceinline__ float times4(float x) { return 4.f * x; }
 
+// 1/x and 1/sqrt(x) for the FP64 path with two thirds of the FP64 operations of
+// the library forms: an FP32 seed (the hardware approximation of a float copy taken
+// on the integer pipe, relative error e ~ 2^-22) and one third-order correction in
+// FP64 -- 1/x = y0 (1 + e + e^2) with e = 1 - x y0, 1/sqrt(x) = y0 (1 + e/2 + 3 e^2/8)
+// with e = 1 - x y0^2 -- whose truncation error (~e^3 < 2^-64) lies below the FP64
+// rounding, so the results are within about one unit in the last place.  An x whose
+// float copy is zero, infinite or not a number (magnitudes beyond the float range,
+// x <= 0 for the square root, NaN) takes the library form.
+__device__ __forceinline__ double rcp64(double x)
+{
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(trunc_f32(x)));
+    if (!(fabsf(yf) < INFINITY && yf != 0.f)) return 1.0 / x;
+    const double y0 = to_f64(yf);
+    const double e = fma(-x, y0, 1.0);
+    return fma(y0, fma(e, e, e), y0);
+}
+__device__ __forceinline__ double rsqrt64(double x)
+{
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(trunc_f32(x)));
+    if (!(yf < INFINITY && yf > 0.f)) return rsqrt(x);
+    const double y0 = to_f64(yf);
+    const double e = fma(-(x * y0), y0, 1.0);
+    return fma(y0, e * fma(0.375, e, 0.5), y0);
+}
+// the precision-generic forms used by the sweeps
+__device__ __forceinline__ double rcp_r(double x) { return rcp64(x); }
+__device__ __forceinline__ float rcp_r(float x) { return 1.f / x; }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt64(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+
 template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return lt(a, b) ? a : b; }
 template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return lt(b, a) ? a : b; }
 
@@ -455,7 +487,7 @@ __device__ __forceinline__ void phys(const R *s, R v2, R gam, R gfac, R *U, R *F
     const R rho = s[0], vx = s[1], vy = s[2], vz = s[3], pg = s[4];
     const R bx = s[5], by = s[6], bz = s[7];
     R omv2 = R(1) - v2;
-    R lor = rsqrt(omv2);
+    R lor = rsqrt_r(omv2);
     R lor2 = lor * lor;
     R rhoh = rho + gfac * pg;
     R w = rhoh * lor2;
@@ -512,7 +544,7 @@ __device__ __forceinline__ void phys(const R *s, R v2, R gam, R gfac, R *U, R *F
     // sqrt(disc)/Y = disc q and 1/Y = Y disc q^2 (disc > 0); disc <= 0 takes 1/Y
     const R a = vd * P;
     if (gtz(disc)) {
-        R q = rsqrt(disc * Y * Y);
+        R q = rsqrt_r(disc * Y * Y);
         R srx = disc * q;
         R inv = Y * srx * q;
         lp = a * inv + srx;
@@ -542,7 +574,7 @@ __device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const
 #pragma unroll
             for (int t = 0; t < 2; t++)
                 e4 += wa[s] * wb[t] * (vb[s][t] * Ba[t] - va[s][t] * Bb[s]);
-        R r = R(1) / (sa * sb);
+        R r = rcp_r(sa * sb);
         e4 = e4 * r;
         isa = sb * r;
         isb = sa * r;
@@ -553,8 +585,8 @@ __device__ __forceinline__ R uct_point(const R va[2][2], const R vb[2][2], const
             for (int t = 0; t < 2; t++)
                 e4 += R(0.25) * (vb[s][t] * Ba[t] - va[s][t] * Bb[s]);
     }
-    if (pa && !pb) isa = R(1) / sa;
-    if (pb && !pa) isb = R(1) / sb;
+    if (pa && !pb) isa = rcp_r(sa);
+    if (pb && !pa) isb = rcp_r(sb);
     R da = apa * ama * (Bb[1] - Bb[0]) * isa;
     R db = apb * amb * (Ba[1] - Ba[0]) * isb;
     return e4 + da - db;
@@ -573,7 +605,7 @@ __device__ __forceinline__ bool c2p_eval(const C2PInv &q, double W, double &v2, 
 {
     if (!gtz(W) || !finite64(W)) return false;
     double wb = W + q.B2;
-    r = 1.0 / (W * wb);
+    r = rcp64(W * wb);
     v2 = (q.S2 * W * W + q.SB * q.SB * (q.B2 + 2.0 * W)) * (r * r);
     return finite64(v2) && lt(v2, 1.0);
 }
@@ -688,7 +720,7 @@ __device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, con
         double wb = W + q.B2;
         double iW = wb * r, iwb = W * r;
         double omv2 = 1.0 - v2;
-        double isq = rsqrt(omv2);
+        double isq = rsqrt64(omv2);
         double sq1 = omv2 * isq;
         double iW2 = iW * iW;
         double p = q.gm1g * (W * omv2 - q.D * sq1);
@@ -700,7 +732,7 @@ __device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, con
         } else {
             double dp = q.gm1g * (omv2 - W * dv2 + 0.5 * q.D * dv2 * isq);
             double df = 1.0 - dp + 0.5 * q.B2 * dv2 + SB2 * (iW2 * iW);
-            dW = -f / df;
+            dW = -f * rcp64(df);
         }
         if (!finite64(dW)) break;
         double lam = 1.0, Wn = W + dW, v2n, rn;
@@ -764,7 +796,8 @@ __device__ __forceinline__ bool c2p_newton(const C2PInv &q, const double *u, con
     Wout = W;
     if (!ok) v2 = fmin(fmax(v2, 0.0), 1.0);
     double omv2 = 1.0 - v2;
-    double sq1 = have_sq1 ? sq1f : sqrt(omv2);
+    // sqrt(1 - v^2) as (1 - v^2)/sqrt(1 - v^2); a clamped v^2 = 1 (failed cell) gives 0
+    double sq1 = have_sq1 ? sq1f : omv2 * rsqrt64(rmax(omv2, 1e-300));
     double p = q.gm1g * (W * omv2 - q.D * sq1);
     double rho = q.D * sq1;
     double wb = W + q.B2;

@@ -309,7 +309,7 @@ k_flux(Grid g, const R *__restrict__ prim, const R *__restrict__ Bf, R *__restri
         const int ncomp = uct ? 5 : 8;  // with UCT the field takes the edge fields instead
         if (gtz(s)) {
             // HLL weights divided once: a+/(a+ + a-), a-/(a+ + a-), a+ a-/(a+ + a-)
-            const R is = R(1) / s;
+            const R is = rcp_r(s);
             const R wl = ap * is, wr = am * is, wd = ap * wr;
 #pragma unroll
             for (int qq = 0; qq < 8; qq++)
