@@ -213,12 +213,14 @@ __device__ __forceinline__ double times4(double x)
 }
 __device__ __forceinline__ float times4(float x) { return 4.f * x; }
 
-// 1/x and 1/sqrt(x) for the FP64 path with two thirds of the FP64 operations of
-// the library forms: an FP32 seed (the hardware approximation of a float copy taken
-// on the integer pipe, relative error e ~ 2^-22) and one third-order correction in
-// FP64 -- 1/x = y0 (1 + e + e^2) with e = 1 - x y0, 1/sqrt(x) = y0 (1 + e/2 + 3 e^2/8)
-// with e = 1 - x y0^2 -- whose truncation error (~e^3 < 2^-64) lies below the FP64
-// rounding, so the results are within about one unit in the last place.  An x whose
+// 1/x and 1/sqrt(x) for the FP64 path with fewer FP64 operations than the library
+// forms: an FP32 seed y0 (the hardware approximation of a float copy taken on the
+// integer pipe, relative error ~2^-22) and one third-order correction in FP64 --
+// Householder's order-3 step, i.e. the series 1/(1 - e) = 1 + e + e^2 + ... with
+// e = 1 - x y0 for 1/x, and (1 - e)^(-1/2) = 1 + e/2 + 3 e^2/8 + ... with e = 1 - x y0^2
+// for 1/sqrt(x) -- whose truncation error (~e^3 < 2^-64) lies below the FP64 rounding,
+// so the results are within about one unit in the last place (tests compare them
+// with CUDA's 1.0/x and rsqrt on the GPU).  An x whose
 // float copy is zero, infinite or not a number (magnitudes beyond the float range,
 // x <= 0 for the square root, NaN) takes the library form.
 __device__ __forceinline__ double rcp64(double x)
